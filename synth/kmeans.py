@@ -1,0 +1,91 @@
+"""Seeded spherical K-means patches (Sec. 2.2): Lloyd iterations on pixel-centre unit vectors.
+
+Assignment is by largest dot product with the centroid directions (smallest angular distance;
+ties go to the lowest cluster index); a centroid is the renormalised mean of its members' unit
+vectors. An emptied cluster is re-seeded at the pixel farthest from its own centroid. The loop stops
+at a fixed point or after `max_iter` iterations; labels are then renumbered 0..K_eff-1 in order of
+first appearance (K_eff <= K). K >= number of pixels gives one pixel per patch (the paper's rule when
+the requested patch count exceeds the available pixels, Table 1 caption).
+
+Used to generate inputs (cluster labels) only.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+_CACHE: dict = {}
+
+
+def _assign(vec, cent, chunk=8192):
+    lab = np.empty(vec.shape[0], dtype=np.int64)
+    best = np.empty(vec.shape[0])
+    for s in range(0, vec.shape[0], chunk):
+        dots = vec[s:s + chunk] @ cent.T
+        lab[s:s + chunk] = np.argmax(dots, axis=1)
+        best[s:s + chunk] = dots[np.arange(dots.shape[0]), lab[s:s + chunk]]
+    return lab, best
+
+
+def spherical_kmeans(vec: np.ndarray, k: int, seed: int, max_iter: int = 30) -> np.ndarray:
+    """Labels (int32, contiguous from 0) of a seeded spherical K-means of unit vectors `vec`."""
+    n = vec.shape[0]
+    if k >= n:
+        return np.arange(n, dtype=np.int32)
+    if k <= 1:
+        return np.zeros(n, dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    cent = vec[rng.choice(n, size=k, replace=False)].copy()
+    labels = None
+    for _ in range(max_iter):
+        new, best = _assign(vec, cent)
+        if labels is not None and np.array_equal(new, labels):
+            break
+        labels = new
+        counts = np.bincount(labels, minlength=k)
+        sums = np.stack([np.bincount(labels, weights=vec[:, c], minlength=k) for c in range(3)], 1)
+        empty = np.nonzero(counts == 0)[0]
+        if empty.size:
+            far = np.argsort(best, kind="stable")[:empty.size]
+            sums[empty] = vec[far]
+        norm = np.linalg.norm(sums, axis=1)
+        norm[norm == 0] = 1.0
+        cent = sums / norm[:, None]
+    _, first = np.unique(labels, return_index=True)
+    order = np.argsort(first, kind="stable")
+    remap = np.empty(k, dtype=np.int64)
+    used = np.unique(labels)[order]
+    remap[used] = np.arange(used.size)
+    return remap[labels].astype(np.int32)
+
+
+def patch_labels(vec: np.ndarray, k: int, key: str = "") -> np.ndarray:
+    """Labels for K patches on the pixel set `vec`, seeded by K (seed 100 + K), memoised.
+
+    Two parameters with the same K share one labeling, as a single K-means seed would give."""
+    ck = (key, vec.shape[0], int(k))
+    if ck not in _CACHE:
+        _CACHE[ck] = spherical_kmeans(vec, int(k), seed=100 + int(k))
+    return _CACHE[ck]
+
+
+def _worker(args):
+    vec, k = args
+    return k, spherical_kmeans(vec, k, seed=100 + k)
+
+
+def many_patch_labels(vec: np.ndarray, ks, key: str = "", processes: int | None = None):
+    """Labelings for every distinct K in `ks` (dict K -> labels), computed in a spawn pool."""
+    todo = sorted({int(k) for k in ks if (key, vec.shape[0], int(k)) not in _CACHE}, reverse=True)
+    if todo:
+        nproc = processes or min(len(todo), len(os.sched_getaffinity(0)))
+        if nproc > 1 and len(todo) > 4:
+            import multiprocessing as mp
+            with mp.get_context("spawn").Pool(nproc) as pool:
+                for k, lab in pool.imap_unordered(_worker, [(vec, k) for k in todo]):
+                    _CACHE[(key, vec.shape[0], k)] = lab
+        else:
+            for k in todo:
+                _CACHE[(key, vec.shape[0], k)] = spherical_kmeans(vec, k, seed=100 + k)
+    return {int(k): _CACHE[(key, vec.shape[0], int(k))] for k in ks}
