@@ -1,0 +1,214 @@
+/*
+ * csx -- clustered parametric component separation on NVIDIA B300 (sm_103a).
+ *
+ * C ABI of the hot path of the parametric spectral-likelihood method of arxiv 2604.08463:
+ * the mixing matrix (Eq. 5), the clustered spectral likelihood (Eq. 4 over the patches of
+ * Sec. 2.2), its adjoint gradient (Sec. 3.3.1), the batched box-bounded fit over patch
+ * configurations x noise realizations (Eq. 7, Sec. 3.1, App. A), and the reconstruction
+ * s_hat = W d with its residual diagnostics (Eqs. 3, 8-11, 14-15).
+ *
+ * Conventions shared by every call
+ *   - Plain pointers and sizes only. "device" pointers are CUDA device memory of the current
+ *     device, "host" pointers are ordinary host memory. The caller owns every buffer; no pointer is
+ *     retained after a call returns.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) unless stated otherwise. Outputs are valid once the stream has been synchronised.
+ *   - Return value: CSX_OK (0) or a negative CSX_E* code; csx_last_error() gives a message.
+ *     No exception or abort crosses the ABI. Argument checks happen before anything is enqueued.
+ *   - The library keeps per-device scratch buffers between calls (grown on demand with
+ *     cudaMalloc, released by csx_release()). Calls that use the same scratch must not overlap
+ *     in time on different streams.
+ *   - Band axis: every per-pixel vector has 16 float slots; bands nfreq..15 must hold zeros.
+ *   - Data d: float32 [nreal][npix][2][16], Stokes Q then U: one 128-byte line per pixel.
+ *   - Patch labels: int32 [3][npix] per configuration (beta_d, T_d, beta_s labelings), values in
+ *     [0, K_j). Labels out of range make the affected problem's likelihood NaN (spectral calls,
+ *     reconstruction) or the fit call return CSX_ELABEL.
+ *   - Parameters of one problem are packed [beta_d (K_d) | T_d (K_T) | beta_s (K_s)], P = sum K_j.
+ */
+#ifndef CSX_H
+#define CSX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSX_MAX_BANDS 16
+#define CSX_NMETRIC 8
+
+/* return codes */
+#define CSX_OK 0
+#define CSX_EINVAL (-1)   /* null pointer, bad size or option */
+#define CSX_ECUDA (-2)    /* a CUDA runtime call failed */
+#define CSX_ENOMEM (-3)   /* scratch allocation failed */
+#define CSX_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define CSX_ELABEL (-5)   /* a label outside [0, K_j) was found */
+
+/* noise models: N_p^-1 = diag(ninv_band) | w_p diag(ninv_band) | diag(ninv_pix[p]) */
+#define CSX_NOISE_HOMOGENEOUS 0
+#define CSX_NOISE_SEPARABLE 1
+#define CSX_NOISE_PERPIXEL 2
+
+/* per-problem fit status */
+#define CSX_FIT_CONVERGED 0
+#define CSX_FIT_MAXITER 1
+#define CSX_FIT_NONPHYSICAL 2   /* non-finite likelihood at the start (e.g. singular A^T N^-1 A) */
+#define CSX_FIT_LINESEARCH 3    /* no acceptable step from the current point */
+
+/* likelihood evaluation inside the fit */
+#define CSX_PATH_AUTO 0
+#define CSX_PATH_STREAM 1  /* per pixel, any noise model */
+#define CSX_PATH_MOMENT 2  /* per cell of equal (l_d, l_T, l_s); separable/homogeneous noise */
+
+/* gradient inside the fit */
+#define CSX_GRAD_ADJOINT 0 /* Sec. 3.3.1 */
+#define CSX_GRAD_FD 1      /* central finite differences of the forward likelihood (plain form) */
+
+/* selection-metric slots of csx_reconstruct (per problem, float64 sums over its pixels) */
+#define CSX_M_SYS_SQ 0      /* sum_{p,s} r_sys^2,  r_sys = [W d_fg]_cmb (Eq. 15) */
+#define CSX_M_STAT 1        /* sum_p [M_p^-1]_00 (statistical residual variance) */
+#define CSX_M_CMB_Q 2       /* sum_p s_hat_cmb,Q */
+#define CSX_M_CMB_Q2 3      /* sum_p s_hat_cmb,Q^2 */
+#define CSX_M_CMB_U 4       /* sum_p s_hat_cmb,U */
+#define CSX_M_CMB_U2 5      /* sum_p s_hat_cmb,U^2 */
+#define CSX_M_NPIX 6        /* number of pixels */
+
+/* Spectral model of Eq. 5: CMB column 1; dust modified blackbody normalised at nu0_dust;
+ * synchrotron power law normalised at nu0_sync. units 0: K_CMB (each foreground column times
+ * g(nu)/g(nu0), g = (e^x-1)^2/(x^2 e^x), x = h nu / k t_cmb); units 1: Rayleigh-Jeans. */
+typedef struct csx_model {
+  int32_t nfreq;          /* 1 .. 15 */
+  int32_t units;          /* 0 K_CMB, 1 RJ */
+  double nu_ghz[CSX_MAX_BANDS];
+  double nu0_dust_ghz;    /* 353 */
+  double nu0_sync_ghz;    /* 23 */
+  double t_cmb;           /* 2.7255 K */
+} csx_model;
+
+/* Data and noise (Eq. 1). */
+typedef struct csx_sky {
+  int32_t npix;
+  int32_t nreal;                       /* realizations stored in d */
+  int32_t noise_kind;                  /* CSX_NOISE_* */
+  int32_t reserved;
+  const float* d;                      /* device [nreal][npix][2][16] */
+  float ninv_band[CSX_MAX_BANDS];      /* host values: 1/sigma_f^2 (HOMOGENEOUS, SEPARABLE) */
+  const float* w;                      /* device [npix] hit-count weights (SEPARABLE), else NULL */
+  const float* ninv_pix;               /* device [npix][16] (PERPIXEL), else NULL */
+} csx_sky;
+
+/* Options of csx_fit_batch. csx_fit_defaults() fills the values quoted here. */
+typedef struct csx_fit_opts {
+  int32_t max_iter;     /* 500: quasi-Newton iterations per problem */
+  int32_t history;      /* 8: L-BFGS memory m, 1..16 */
+  int32_t max_ls;       /* 20: likelihood evaluations per line search */
+  int32_t path;         /* CSX_PATH_AUTO */
+  int32_t grad_mode;    /* CSX_GRAD_ADJOINT */
+  int32_t threads;      /* 0 = automatic CTA size */
+  float lower[3];       /* box bounds (beta_d, T_d [K], beta_s): 0.5, 5, -5 */
+  float upper[3];       /* 3, 60, -1 */
+  float xtol[3];        /* 1e-4, 1e-3 K, 1e-4: stop once the quasi-Newton step and the last step of
+                           every free parameter are below these (physical units) */
+  float fd_step;        /* 1e-3: central-difference step in Gauss-Newton-scaled units (FD mode) */
+} csx_fit_opts;
+
+/* Library version string. */
+const char* csx_version(void);
+
+/* Message of the last error on this host thread ("" if none). */
+const char* csx_last_error(void);
+
+/* Free the scratch buffers of the current device. Synchronises the device. */
+int csx_release(void);
+
+/* Fill `o` with the defaults listed in csx_fit_opts. */
+int csx_fit_defaults(csx_fit_opts* o);
+
+/*
+ * Mixing matrix and its parameter derivatives (Eq. 5) for n parameter triples.
+ *   beta  device float [n][3]  (beta_d, T_d [K], beta_s)
+ *   A     device float [n][16][3]  (bands >= nfreq are 0)
+ *   dA    device float [n][3][16] or NULL: dA_dust/dbeta_d, dA_dust/dT_d, dA_sync/dbeta_s
+ * T_d <= 0 gives NaN entries.
+ */
+int csx_mixing(const csx_model* m, int32_t n, const float* beta, float* A, float* dA, void* stream);
+
+/*
+ * Spectral likelihood L(beta) = - sum_p sum_{s=Q,U} (A^T N^-1 d)^T (A^T N^-1 A)^-1 (A^T N^-1 d)
+ * (Eq. 4, negated and doubled), for one patch configuration and nprob problems; problem i uses
+ * realization i of the sky (nprob <= sky->nreal) and its own parameters.
+ *   labels device int32 [3][npix];  K host int32[3]
+ *   beta   device float [nprob][P]
+ *   L      device double [nprob]   (overwritten)
+ * Streaming kernel over pixels, evaluated in the residual form L = chi2_min - sum d^T N^-1 d.
+ * A pixel whose A^T N^-1 A is not positive definite makes its problem's L NaN.
+ */
+int csx_spectral_like(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                      const int32_t K[3], int32_t nprob, const float* beta, double* L,
+                      void* stream);
+
+/*
+ * Likelihood and adjoint gradient (Sec. 3.3.1): dL/dbeta = -2 sum_p sum_s w_r^T (dA/dbeta) s_hat,
+ * w_r = N^-1 (d - A s_hat), routed to the owning patch. Same arguments as csx_spectral_like plus
+ *   L     device double [nprob] or NULL
+ *   grad  device float [nprob][P]  (overwritten)
+ */
+int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                      const int32_t K[3], int32_t nprob, const float* beta, double* L,
+                      float* grad, void* stream);
+
+/*
+ * Cells of each configuration: pixels sorted stably by (l_d, l_T, l_s) (Sec. 2.2-2.3).
+ *   labels   device int32 [nconf][3][npix];  K host int32 [nconf][3]
+ *   perm     device int32 [nconf][npix]      sorted pixel indices
+ *   cell_off device int32 [nconf][npix + 1]  start of each cell in perm; entries past ncell unused
+ *   ncell    device int32 [nconf]            (-1 for a configuration with a label out of range)
+ * Bit-exact: equals a stable lexicographic sort on the host.
+ */
+int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const int32_t* K,
+                    int32_t* perm, int32_t* cell_off, int32_t* ncell, void* stream);
+
+/*
+ * Batched box-bounded fit beta* = argmin L (Eq. 7) of nconf configurations x sky->nreal
+ * realizations in one persistent launch; problem q = c * nreal + n.
+ *   labels  device int32 [nconf][3][npix];  K host int32 [nconf][3]
+ *   beta0, beta_out  device float, packed per problem: problem q starts at
+ *           nreal * coff[c] + n * P_c with coff[c] = sum_{c' < c} P_c' (beta_out may alias beta0)
+ *   L_out   device double [nconf * nreal] (L at beta_out), status / iters device int32 [nconf*nreal]
+ * Optimiser: L-BFGS in Gauss-Newton-scaled variables with the active-set bound handling and
+ * step limit of App. A, line search on approximate Wolfe conditions. With the moment path the call
+ * synchronises `stream` once (to read the cell counts).
+ */
+int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
+                  const int32_t* K, const csx_fit_opts* opts, const float* beta0, float* beta_out,
+                  double* L_out, int32_t* status, int32_t* iters, void* stream);
+
+/*
+ * Reconstruction s_hat = W d, W = (A^T N^-1 A)^-1 A^T N^-1 (Eqs. 3, 8) and residual diagnostics
+ * for nconf configurations x sky->nreal realizations at the parameters `beta` (packed as in
+ * csx_fit_batch). Every output may be NULL.
+ *   d_fg    device float [npix][2][16] noise-free foreground data, or NULL (no r_sys)
+ *   s_hat   device float [nconf*nreal][npix][2][3]
+ *   sigma2  device float [nconf*nreal][npix]      [M_p^-1]_00
+ *   r_sys   device float [nconf*nreal][npix][2]   [W d_fg]_cmb (Eq. 15)
+ *   metrics device double [nconf*nreal][CSX_NMETRIC]  (CSX_M_* slots, overwritten)
+ */
+int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
+                    const int32_t* K, const float* beta, const float* d_fg, float* s_hat,
+                    float* sigma2, float* r_sys, double* metrics, void* stream);
+
+/*
+ * Selection over configurations by total residual variance:
+ *   vtot[c] = mean_n ( metrics[c,n][SYS_SQ] / (2 npix) + metrics[c,n][STAT] / npix ),
+ *   best = argmin_c vtot[c] (lowest index on ties; NaN never wins).
+ *   metrics device double [nconf*nreal][CSX_NMETRIC]; vtot device double [nconf]; best device int32[1]
+ */
+int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot, int32_t* best,
+               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSX_H */

@@ -1,0 +1,494 @@
+// C ABI of the csx library (include/csx.h): argument checks, per-device scratch, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "csx_host.h"
+
+namespace csx {
+
+// ------------------------------------------------------------------------------ errors ---------
+static thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? CSX_ENOMEM : CSX_ECUDA;
+}
+
+// ------------------------------------------------------------------------------ scratch --------
+namespace {
+constexpr int kMaxDev = 64;
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+std::mutex g_mu;
+Buf g_buf[kMaxDev][SCR_COUNT];
+}  // namespace
+
+void* scratch(ScratchId id, size_t bytes, int* err) {
+  int dev = 0;
+  *err = CSX_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    *err = fail(CSX_ECUDA, "cudaGetDevice failed");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  Buf& b = g_buf[dev][id];
+  if (bytes == 0) bytes = 1;
+  if (b.n < bytes) {
+    if (b.p) {
+      cudaError_t e = cudaFree(b.p);
+      b.p = nullptr;
+      b.n = 0;
+      if (e != cudaSuccess) {
+        *err = cuda_fail(e, "cudaFree(scratch)");
+        return nullptr;
+      }
+    }
+    const size_t want = bytes + bytes / 4;  // headroom against repeated growth
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      *err = cuda_fail(e, "cudaMalloc(scratch)");
+      return nullptr;
+    }
+    b.n = want;
+  }
+  return b.p;
+}
+
+void scratch_release_all() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (int i = 0; i < SCR_COUNT; ++i) {
+    if (g_buf[dev][i].p) cudaFree(g_buf[dev][i].p);
+    g_buf[dev][i] = Buf();
+  }
+}
+
+// ------------------------------------------------------------------------------ model ----------
+// RJ -> K_CMB factor u(nu) = (e^x - 1)^2 / (x^2 e^x), x = h nu / (k T_CMB).
+static double rj_to_kcmb(double nu_ghz, double t_cmb) {
+  const double h_over_k = 6.62607015e-34 / 1.380649e-23 * 1e9;  // K per GHz
+  const double x = h_over_k * nu_ghz / t_cmb;
+  const double em1 = std::expm1(x);
+  return em1 * em1 / (x * x * std::exp(x));
+}
+
+Bands make_bands(const csx_model& m) {
+  Bands b;
+  std::memset(&b, 0, sizeof(b));
+  const double h_over_k = 6.62607015e-34 / 1.380649e-23 * 1e9;
+  b.nf = m.nfreq;
+  b.xk0 = (float)(h_over_k * m.nu0_dust_ghz);
+  const bool kcmb = (m.units == 0);
+  const double ud = kcmb ? rj_to_kcmb(m.nu0_dust_ghz, m.t_cmb) : 1.0;
+  const double us = kcmb ? rj_to_kcmb(m.nu0_sync_ghz, m.t_cmb) : 1.0;
+  for (int f = 0; f < m.nfreq; ++f) {
+    const double nu = m.nu_ghz[f];
+    const double u = kcmb ? rj_to_kcmb(nu, m.t_cmb) : 1.0;
+    b.lnd[f] = (float)std::log(nu / m.nu0_dust_ghz);
+    b.lns[f] = (float)std::log(nu / m.nu0_sync_ghz);
+    b.xk[f] = (float)(h_over_k * nu);
+    b.cd[f] = (float)(nu / m.nu0_dust_ghz * u / ud);
+    b.cs[f] = (float)(u / us);
+  }
+  return b;
+}
+
+// ------------------------------------------------------------------------------ checks ---------
+static int check_model(const csx_model* m) {
+  if (!m) return fail(CSX_EINVAL, "model is NULL");
+  if (m->nfreq < 1 || m->nfreq > 15) return fail(CSX_EINVAL, "nfreq must be in 1..15");
+  if (m->units != 0 && m->units != 1) return fail(CSX_EINVAL, "units must be 0 (K_CMB) or 1 (RJ)");
+  if (!(m->nu0_dust_ghz > 0) || !(m->nu0_sync_ghz > 0)) return fail(CSX_EINVAL, "reference frequencies must be > 0");
+  if (m->units == 0 && !(m->t_cmb > 0)) return fail(CSX_EINVAL, "t_cmb must be > 0 for K_CMB units");
+  for (int f = 0; f < m->nfreq; ++f)
+    if (!(m->nu_ghz[f] > 0)) return fail(CSX_EINVAL, "band frequencies must be > 0");
+  return CSX_OK;
+}
+
+static int check_sky(const csx_sky* s, int nfreq) {
+  if (!s) return fail(CSX_EINVAL, "sky is NULL");
+  if (s->npix < 0 || s->nreal < 0) return fail(CSX_EINVAL, "npix and nreal must be >= 0");
+  if (s->npix > 0 && s->nreal > 0 && !s->d) return fail(CSX_EINVAL, "sky->d is NULL");
+  if (s->noise_kind < 0 || s->noise_kind > 2) return fail(CSX_EINVAL, "unknown noise_kind");
+  if (s->noise_kind == CSX_NOISE_SEPARABLE && !s->w && s->npix > 0)
+    return fail(CSX_EINVAL, "separable noise needs sky->w");
+  if (s->noise_kind == CSX_NOISE_PERPIXEL && !s->ninv_pix && s->npix > 0)
+    return fail(CSX_EINVAL, "per-pixel noise needs sky->ninv_pix");
+  if (s->noise_kind != CSX_NOISE_PERPIXEL) {
+    for (int f = 0; f < nfreq; ++f)
+      if (!(s->ninv_band[f] >= 0.f) || !std::isfinite(s->ninv_band[f]))
+        return fail(CSX_EINVAL, "ninv_band must be finite and >= 0");
+  }
+  return CSX_OK;
+}
+
+static int check_K(const int32_t* K) {
+  for (int j = 0; j < 3; ++j)
+    if (K[j] < 1) return fail(CSX_EINVAL, "every K_j must be >= 1");
+  return CSX_OK;
+}
+
+static void copy_band_weights(const csx_sky* s, int nfreq, float* out) {
+  for (int f = 0; f < NB; ++f) out[f] = (f < nfreq) ? s->ninv_band[f] : 0.f;
+}
+
+}  // namespace csx
+
+using namespace csx;
+
+extern "C" {
+
+const char* csx_version(void) { return "csx 0.1.0 (sm_103a)"; }
+
+const char* csx_last_error(void) { return g_err.c_str(); }
+
+int csx_release(void) {
+  CSX_CUDA(cudaDeviceSynchronize());
+  scratch_release_all();
+  return CSX_OK;
+}
+
+int csx_fit_defaults(csx_fit_opts* o) {
+  if (!o) return fail(CSX_EINVAL, "opts is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->max_iter = 500;
+  o->history = 8;
+  o->max_ls = 20;
+  o->path = CSX_PATH_AUTO;
+  o->grad_mode = CSX_GRAD_ADJOINT;
+  o->threads = 0;
+  const float lo[3] = {0.5f, 5.f, -5.f}, hi[3] = {3.f, 60.f, -1.f}, xt[3] = {1e-4f, 1e-3f, 1e-4f};
+  for (int j = 0; j < 3; ++j) {
+    o->lower[j] = lo[j];
+    o->upper[j] = hi[j];
+    o->xtol[j] = xt[j];
+  }
+  o->fd_step = 1e-3f;
+  return CSX_OK;
+}
+
+int csx_mixing(const csx_model* m, int32_t n, const float* beta, float* A, float* dA, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if (n < 0) return fail(CSX_EINVAL, "n must be >= 0");
+  if (n > 0 && (!beta || !A)) return fail(CSX_EINVAL, "beta and A must not be NULL");
+  return launch_mixing(make_bands(*m), n, beta, A, dA, (cudaStream_t)stream);
+}
+
+static int spectral_common(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                           const int32_t K[3], int32_t nprob, const float* beta, double* L,
+                           float* grad, bool want_grad, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (!K) return fail(CSX_EINVAL, "K is NULL");
+  if ((rc = check_K(K))) return rc;
+  if (nprob < 0 || nprob > sky->nreal) return fail(CSX_EINVAL, "nprob must be in [0, sky->nreal]");
+  if (nprob == 0) return CSX_OK;
+  if (!beta) return fail(CSX_EINVAL, "beta is NULL");
+  if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  if (want_grad && !grad) return fail(CSX_EINVAL, "grad is NULL");
+  if (!want_grad && !L) return fail(CSX_EINVAL, "L is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int P = K[0] + K[1] + K[2];
+  const int rows = K[0] + 2 * K[1] + K[2];
+  const Bands b = make_bands(*m);
+  float* tables = (float*)scratch(SCR_TABLES, (size_t)nprob * rows * NB * sizeof(float), &rc);
+  if (rc) return rc;
+  double* Lbuf = L;
+  if (!Lbuf) {
+    Lbuf = (double*)scratch(SCR_MISC, (size_t)nprob * sizeof(double), &rc);
+    if (rc) return rc;
+  }
+  if ((rc = launch_tables(b, nprob, K[0], K[1], K[2], beta, tables, s))) return rc;
+  CSX_CUDA(cudaMemsetAsync(Lbuf, 0, (size_t)nprob * sizeof(double), s));
+  if (want_grad) CSX_CUDA(cudaMemsetAsync(grad, 0, (size_t)nprob * P * sizeof(float), s));
+  SpecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = b;
+  a.npix = sky->npix;
+  a.nprob = nprob;
+  a.Kd = K[0];
+  a.KT = K[1];
+  a.Ks = K[2];
+  a.P = P;
+  a.rows = rows;
+  a.noise_kind = sky->noise_kind;
+  a.d = sky->d;
+  a.w = sky->w;
+  a.ninv_pix = sky->ninv_pix;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.labels = labels;
+  a.beta = beta;
+  a.tables = tables;
+  a.L = Lbuf;
+  a.grad = want_grad ? grad : nullptr;
+  if (sky->npix == 0) return CSX_OK;
+  return launch_spectral(a, want_grad, s);
+}
+
+int csx_spectral_like(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                      const int32_t K[3], int32_t nprob, const float* beta, double* L, void* stream) {
+  return spectral_common(m, sky, labels, K, nprob, beta, L, nullptr, false, stream);
+}
+
+int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                      const int32_t K[3], int32_t nprob, const float* beta, double* L, float* grad,
+                      void* stream) {
+  return spectral_common(m, sky, labels, K, nprob, beta, L, grad, true, stream);
+}
+
+int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const int32_t* K,
+                    int32_t* perm, int32_t* cell_off, int32_t* ncell, void* stream) {
+  if (npix < 0 || nconf < 0) return fail(CSX_EINVAL, "npix and nconf must be >= 0");
+  if (nconf == 0) return CSX_OK;
+  if (!K || !perm || !cell_off || !ncell || (npix > 0 && !labels))
+    return fail(CSX_EINVAL, "NULL argument");
+  for (int c = 0; c < nconf; ++c) {
+    int rc = check_K(K + 3 * c);
+    if (rc) return rc;
+  }
+  int rc = CSX_OK;
+  int* Kd = (int*)scratch(SCR_MISC, (size_t)nconf * 3 * sizeof(int), &rc);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CSX_CUDA(cudaMemcpyAsync(Kd, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+  return launch_cells(npix, nconf, labels, Kd, perm, cell_off, ncell, s);
+}
+
+int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
+                  const int32_t* K, const csx_fit_opts* opts, const float* beta0, float* beta_out,
+                  double* L_out, int32_t* status, int32_t* iters, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (nconf < 0) return fail(CSX_EINVAL, "nconf must be >= 0");
+  const long long nprob = (long long)nconf * sky->nreal;
+  if (nprob == 0) return CSX_OK;
+  if (nprob > (1LL << 30)) return fail(CSX_EINVAL, "too many problems");
+  if (!K || !opts || !beta0 || !beta_out || !L_out || !status || !iters)
+    return fail(CSX_EINVAL, "NULL argument");
+  if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  const csx_fit_opts& o = *opts;
+  if (o.history < 1 || o.history > 16) return fail(CSX_EINVAL, "history must be in 1..16");
+  if (o.max_iter < 0 || o.max_ls < 1) return fail(CSX_EINVAL, "max_iter >= 0 and max_ls >= 1 required");
+  if (o.grad_mode != CSX_GRAD_ADJOINT && o.grad_mode != CSX_GRAD_FD) return fail(CSX_EINVAL, "unknown grad_mode");
+  for (int j = 0; j < 3; ++j) {
+    if (!(o.lower[j] < o.upper[j])) return fail(CSX_EINVAL, "lower < upper required");
+    if (!(o.xtol[j] > 0)) return fail(CSX_EINVAL, "xtol must be > 0");
+  }
+  if (o.lower[1] <= 0.f) return fail(CSX_EINVAL, "T_d lower bound must be > 0");
+  if (o.grad_mode == CSX_GRAD_FD && !(o.fd_step > 0)) return fail(CSX_EINVAL, "fd_step must be > 0");
+  int path = o.path;
+  if (path == CSX_PATH_AUTO)
+    path = (sky->noise_kind != CSX_NOISE_PERPIXEL && o.grad_mode == CSX_GRAD_ADJOINT) ? CSX_PATH_MOMENT
+                                                                                     : CSX_PATH_STREAM;
+  if (path != CSX_PATH_MOMENT && path != CSX_PATH_STREAM) return fail(CSX_EINVAL, "unknown path");
+  if (path == CSX_PATH_MOMENT && sky->noise_kind == CSX_NOISE_PERPIXEL)
+    return fail(CSX_EINVAL, "the moment path needs homogeneous or separable noise");
+  if (path == CSX_PATH_MOMENT && o.grad_mode == CSX_GRAD_FD)
+    return fail(CSX_EINVAL, "the finite-difference plain form uses the stream path");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int npix = sky->npix;
+
+  // problem descriptors
+  std::vector<long long> coff(nconf + 1, 0);
+  int Pmax = 0, rows_max = 0;
+  for (int c = 0; c < nconf; ++c) {
+    if ((rc = check_K(K + 3 * c))) return rc;
+    const int P = K[3 * c] + K[3 * c + 1] + K[3 * c + 2];
+    coff[c + 1] = coff[c] + P;
+    Pmax = std::max(Pmax, P);
+    rows_max = std::max(rows_max, K[3 * c] + 2 * K[3 * c + 1] + K[3 * c + 2]);
+  }
+  Pmax = (Pmax + 3) & ~3;
+  std::vector<ProbDesc> probs((size_t)nprob);
+  for (int c = 0; c < nconf; ++c)
+    for (int n = 0; n < sky->nreal; ++n) {
+      ProbDesc& d = probs[(size_t)c * sky->nreal + n];
+      d.conf = c;
+      d.real = n;
+      d.Kd = K[3 * c];
+      d.KT = K[3 * c + 1];
+      d.Ks = K[3 * c + 2];
+      d.P = d.Kd + d.KT + d.Ks;
+      d.poff = (long long)sky->nreal * coff[c] + (long long)n * d.P;
+      d.toff = 0;
+    }
+
+  // cells (moment path): built on the device, counts read back to size the per-slot scratch
+  int ncell_max = 0;
+  int *perm = nullptr, *coffs = nullptr, *ncell = nullptr;
+  std::vector<int> ncell_h(nconf, 0);
+  if (path == CSX_PATH_MOMENT) {
+    const size_t per = (size_t)npix;
+    char* cb = (char*)scratch(SCR_CELLS, (size_t)nconf * (2 * per + 1) * sizeof(int) + (size_t)nconf * 4 * sizeof(int) + 256, &rc);
+    if (rc) return rc;
+    perm = (int*)cb;
+    coffs = perm + (size_t)nconf * per;
+    ncell = coffs + (size_t)nconf * (per + 1);
+    int* Kdev = ncell + nconf;
+    CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+    if ((rc = launch_cells(npix, nconf, labels, Kdev, perm, coffs, ncell, s))) return rc;
+    CSX_CUDA(cudaMemcpyAsync(ncell_h.data(), ncell, (size_t)nconf * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CSX_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < nconf; ++c) {
+      if (ncell_h[c] < 0) return fail(CSX_ELABEL, "configuration " + std::to_string(c) + " has a label outside [0, K_j)");
+      ncell_max = std::max(ncell_max, ncell_h[c]);
+    }
+  }
+
+  // largest-first queue order (longest processing time first)
+  std::vector<int> order((size_t)nprob);
+  std::iota(order.begin(), order.end(), 0);
+  std::vector<double> cost((size_t)nprob);
+  for (long long q = 0; q < nprob; ++q) {
+    const ProbDesc& d = probs[(size_t)q];
+    cost[(size_t)q] = (path == CSX_PATH_MOMENT) ? (double)ncell_h[d.conf] + 8.0 * d.P : (double)d.P;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+
+  char* db = (char*)scratch(SCR_FIT_DESC, (size_t)nprob * (sizeof(ProbDesc) + sizeof(int)) + 64, &rc);
+  if (rc) return rc;
+  ProbDesc* probs_d = (ProbDesc*)db;
+  int* order_d = (int*)(db + (size_t)nprob * sizeof(ProbDesc));
+  int* head_d = order_d + nprob;
+  CSX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), (size_t)nprob * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  CSX_CUDA(cudaMemcpyAsync(order_d, order.data(), (size_t)nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+
+  long long slot_floats = 0;
+  fit_slot_floats(Pmax, rows_max, ncell_max, o.history, path, &slot_floats);
+  int grid = 0;
+  if ((rc = fit_grid(o.threads, path, o.grad_mode, &grid))) return rc;
+  if ((long long)grid > nprob) grid = (int)nprob;
+  float* slots = (float*)scratch(SCR_FIT_SLOTS, (size_t)grid * slot_floats * sizeof(float), &rc);
+  if (rc) return rc;
+
+  FitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = make_bands(*m);
+  a.npix = npix;
+  a.nreal = sky->nreal;
+  a.noise_kind = sky->noise_kind;
+  a.d = sky->d;
+  a.w = sky->w;
+  a.ninv_pix = sky->ninv_pix;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.labels = labels;
+  a.perm = perm;
+  a.cell_off = coffs;
+  a.ncell = ncell;
+  a.probs = probs_d;
+  a.order = order_d;
+  a.nprob = (int)nprob;
+  a.head = head_d;
+  a.beta0 = beta0;
+  a.beta_out = beta_out;
+  a.L_out = L_out;
+  a.status = status;
+  a.iters = iters;
+  a.slots = slots;
+  a.slot_floats = slot_floats;
+  a.Pmax = Pmax;
+  a.rows_max = rows_max;
+  a.ncell_max = ncell_max;
+  a.history = o.history;
+  a.max_iter = o.max_iter;
+  a.max_ls = o.max_ls;
+  a.path = path;
+  a.grad_mode = o.grad_mode;
+  for (int j = 0; j < 3; ++j) {
+    a.lower[j] = o.lower[j];
+    a.upper[j] = o.upper[j];
+    a.xtol[j] = o.xtol[j];
+  }
+  a.fd_step = o.fd_step;
+  return launch_fit(a, o.threads, grid, s);
+}
+
+int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
+                    const int32_t* K, const float* beta, const float* d_fg, float* s_hat,
+                    float* sigma2, float* r_sys, double* metrics, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (nconf < 0) return fail(CSX_EINVAL, "nconf must be >= 0");
+  const long long nprob = (long long)nconf * sky->nreal;
+  if (nprob == 0) return CSX_OK;
+  if (!K || !beta) return fail(CSX_EINVAL, "NULL argument");
+  if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<ProbDesc> probs((size_t)nprob);
+  long long poff = 0, toff = 0;
+  for (int c = 0; c < nconf; ++c) {
+    if ((rc = check_K(K + 3 * c))) return rc;
+    for (int n = 0; n < sky->nreal; ++n) {
+      ProbDesc& d = probs[(size_t)c * sky->nreal + n];
+      d.conf = c;
+      d.real = n;
+      d.Kd = K[3 * c];
+      d.KT = K[3 * c + 1];
+      d.Ks = K[3 * c + 2];
+      d.P = d.Kd + d.KT + d.Ks;
+      d.poff = poff;
+      d.toff = toff;
+      poff += d.P;
+      toff += d.Kd + 2 * d.KT + d.Ks;
+    }
+  }
+  char* db = (char*)scratch(SCR_RECON_DESC, (size_t)nprob * sizeof(ProbDesc), &rc);
+  if (rc) return rc;
+  ProbDesc* probs_d = (ProbDesc*)db;
+  float* tables = (float*)scratch(SCR_TABLES, (size_t)toff * NB * sizeof(float), &rc);
+  if (rc) return rc;
+  CSX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), (size_t)nprob * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  const Bands b = make_bands(*m);
+  if ((rc = launch_recon_tables(b, (int)nprob, probs_d, beta, tables, toff, s))) return rc;
+  if (metrics) CSX_CUDA(cudaMemsetAsync(metrics, 0, (size_t)nprob * CSX_NMETRIC * sizeof(double), s));
+  if (sky->npix == 0) return CSX_OK;
+  ReconArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = b;
+  a.npix = sky->npix;
+  a.nreal = sky->nreal;
+  a.noise_kind = sky->noise_kind;
+  a.nprob = (int)nprob;
+  a.d = sky->d;
+  a.w = sky->w;
+  a.ninv_pix = sky->ninv_pix;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.labels = labels;
+  a.probs = probs_d;
+  a.tables = tables;
+  a.d_fg = d_fg;
+  a.s_hat = s_hat;
+  a.sigma2 = sigma2;
+  a.r_sys = r_sys;
+  a.metrics = metrics;
+  return launch_recon(a, s);
+}
+
+int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot, int32_t* best,
+               void* stream) {
+  if (nconf < 1 || nreal < 1) return fail(CSX_EINVAL, "nconf and nreal must be >= 1");
+  if (!metrics || !vtot || !best) return fail(CSX_EINVAL, "NULL argument");
+  return launch_select(nconf, nreal, metrics, vtot, best, (cudaStream_t)stream);
+}
+
+}  // extern "C"

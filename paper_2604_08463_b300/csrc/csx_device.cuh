@@ -1,0 +1,288 @@
+// Device building blocks shared by the csx kernels: band constants, SED tables (Eq. 5),
+// the per-pixel residual-form likelihood/gradient (Eqs. 3-4, Sec. 3.3.1), a 3x3 Cholesky
+// solve and block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/csx.h"
+
+namespace csx {
+
+constexpr int NB = 16;     // padded band slots per pixel vector
+constexpr int NE = 120;    // unique entries of a symmetric 15x15 band moment
+
+// Per-band constants of the spectral model, computed on the host in double from csx_model.
+struct Bands {
+  int nf;
+  float xk0;          // h nu0_dust / k  [K]
+  float lnd[NB];      // ln(nu_f / nu0_dust)           (0 for f >= nf)
+  float lns[NB];      // ln(nu_f / nu0_sync)
+  float xk[NB];       // h nu_f / k  [K]
+  float cd[NB];       // (nu_f / nu0_dust) * u_f / u_dust   (u = RJ->K_CMB factor, 1 in RJ units)
+  float cs[NB];       // u_f / u_sync
+};
+
+// ---------------------------------------------------------------------------------------------
+// SED tables. Rows of a problem with (Kd, KT, Ks) patches, 16 floats each:
+//   [0, Kd)            P_d[k][f] = (nu_f/nu0_d)^beta_d,k
+//   [Kd, Kd+KT)        B[j][f]   = (nu_f/nu0_d) (e^{x0}-1)/(e^{x_f}-1) u_f/u_d,  x = h nu / k T_d,j
+//   [Kd+KT, Kd+2KT)    D[j][f]   = d ln B / dT = [x_f/(1-e^{-x_f}) - x0/(1-e^{-x0})] / T_d,j
+//   [Kd+2KT, +Ks)      S[k][f]   = (nu_f/nu0_s)^beta_s,k u_f/u_s
+// so that the dust column is A_d = P_d[l_d] * B[l_T] and the synchrotron column A_s = S[l_s].
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float nan_f() { return __int_as_float(0x7fffffff); }
+
+__device__ __forceinline__ float table_entry(const Bands& b, int row, int f, int Kd, int KT,
+                                             const float* __restrict__ x) {
+  if (f >= b.nf) return 0.f;
+  if (row < Kd) return expf(x[row] * b.lnd[f]);
+  row -= Kd;
+  if (row < KT) {
+    const float T = x[Kd + row];
+    if (!(T > 0.f)) return nan_f();
+    return b.cd[f] * expm1f(b.xk0 / T) / expm1f(b.xk[f] / T);
+  }
+  row -= KT;
+  if (row < KT) {
+    const float T = x[Kd + row];
+    if (!(T > 0.f)) return nan_f();
+    const float xf = b.xk[f] / T, x0 = b.xk0 / T;
+    return (xf / -expm1f(-xf) - x0 / -expm1f(-x0)) / T;
+  }
+  row -= KT;
+  return b.cs[f] * expf(x[Kd + KT + row] * b.lns[f]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// 3x3 symmetric positive-definite factorisation M = L L^T (lower L, inverse diagonal kept).
+// ---------------------------------------------------------------------------------------------
+struct Chol3 {
+  float l10, l20, l21, i00, i11, i22;
+};
+
+__device__ __forceinline__ bool chol3(float m00, float m01, float m02, float m11, float m12,
+                                      float m22, Chol3& c) {
+  if (!(m00 > 0.f)) return false;
+  const float l00 = sqrtf(m00);
+  c.i00 = 1.f / l00;
+  c.l10 = m01 * c.i00;
+  c.l20 = m02 * c.i00;
+  const float t11 = fmaf(-c.l10, c.l10, m11);
+  if (!(t11 > 0.f)) return false;
+  const float l11 = sqrtf(t11);
+  c.i11 = 1.f / l11;
+  c.l21 = fmaf(-c.l20, c.l10, m12) * c.i11;
+  const float t22 = fmaf(-c.l21, c.l21, fmaf(-c.l20, c.l20, m22));
+  if (!(t22 > 0.f)) return false;
+  c.i22 = 1.f / sqrtf(t22);
+  return true;
+}
+
+// Solve M s = b with the factor of M.
+__device__ __forceinline__ void chol3_solve(const Chol3& c, float b0, float b1, float b2,
+                                            float& s0, float& s1, float& s2) {
+  const float y0 = b0 * c.i00;
+  const float y1 = fmaf(-c.l10, y0, b1) * c.i11;
+  const float y2 = fmaf(-c.l21, y1, fmaf(-c.l20, y0, b2)) * c.i22;
+  s2 = y2 * c.i22;
+  s1 = fmaf(-c.l21, s2, y1) * c.i11;
+  s0 = fmaf(-c.l20, s2, fmaf(-c.l10, s1, y0)) * c.i00;
+}
+
+// Symmetric inverse of M from its factor: returns (v00, v01, v02, v11, v12, v22).
+__device__ __forceinline__ void chol3_inverse(const Chol3& c, float& v00, float& v01, float& v02,
+                                              float& v11, float& v12, float& v22) {
+  // L^-1 (lower): a00, a10, a11, a20, a21, a22
+  const float a00 = c.i00, a11 = c.i11, a22 = c.i22;
+  const float a10 = -c.l10 * a00 * a11;
+  const float a21 = -c.l21 * a11 * a22;
+  const float a20 = -(c.l20 * a00 + c.l21 * a10) * a22;
+  // M^-1 = L^-T L^-1
+  v00 = a00 * a00 + a10 * a10 + a20 * a20;
+  v01 = a10 * a11 + a20 * a21;
+  v02 = a20 * a22;
+  v11 = a11 * a11 + a21 * a21;
+  v12 = a21 * a22;
+  v22 = a22 * a22;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-pixel likelihood in the residual form and adjoint gradient contributions.
+//   M = A^T N A, b_s = A^T N d_s, s_hat = M^-1 b_s, r_s = d_s - A s_hat,
+//   chi2 = sum_s r_s^T N r_s, dnd = sum_s d_s^T N d_s  (L_pixel = chi2 - dnd),
+//   dL/dtheta = -2 sum_s (N r_s)^T (dA/dtheta) s_hat_s   (Sec. 3.3.1)
+// with dA_d/dbeta_d = A_d ln(nu/nu0_d), dA_d/dT_d = A_d D, dA_s/dbeta_s = A_s ln(nu/nu0_s).
+// Optional Gauss-Newton diagonal h_theta = 2 sum_s s_hat_s,k^2 (dA/dtheta)^T N (dA/dtheta).
+// Returns false when M is not positive definite (the caller turns that into NaN).
+// ---------------------------------------------------------------------------------------------
+struct PixOut {
+  float chi2, dnd;
+  float gbd, gtd, gbs;
+  float hbd, htd, hbs;
+};
+
+template <bool GRAD, bool HESS>
+__device__ __forceinline__ bool pixel_eval(const float (&dq)[NB], const float (&du)[NB],
+                                           const float (&nn)[NB], const float* __restrict__ pd,
+                                           const float* __restrict__ bt,
+                                           const float* __restrict__ dt,
+                                           const float* __restrict__ ss, const Bands& bc,
+                                           PixOut& o) {
+  float ad[NB], as[NB];
+  float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
+  float bq0 = 0.f, bq1 = 0.f, bq2 = 0.f, bu0 = 0.f, bu1 = 0.f, bu2 = 0.f;
+  float dnd = 0.f;
+#pragma unroll
+  for (int f4 = 0; f4 < NB; f4 += 4) {
+    const float4 p4 = *reinterpret_cast<const float4*>(pd + f4);
+    const float4 b4 = *reinterpret_cast<const float4*>(bt + f4);
+    const float4 s4 = *reinterpret_cast<const float4*>(ss + f4);
+    ad[f4 + 0] = p4.x * b4.x; ad[f4 + 1] = p4.y * b4.y;
+    ad[f4 + 2] = p4.z * b4.z; ad[f4 + 3] = p4.w * b4.w;
+    as[f4 + 0] = s4.x; as[f4 + 1] = s4.y; as[f4 + 2] = s4.z; as[f4 + 3] = s4.w;
+  }
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    const float n = nn[f];
+    const float na1 = n * ad[f], na2 = n * as[f];
+    m00 += n;
+    m01 += na1;
+    m02 += na2;
+    m11 = fmaf(na1, ad[f], m11);
+    m12 = fmaf(na1, as[f], m12);
+    m22 = fmaf(na2, as[f], m22);
+    const float nq = n * dq[f], nu = n * du[f];
+    bq0 += nq;
+    bq1 = fmaf(na1, dq[f], bq1);
+    bq2 = fmaf(na2, dq[f], bq2);
+    bu0 += nu;
+    bu1 = fmaf(na1, du[f], bu1);
+    bu2 = fmaf(na2, du[f], bu2);
+    dnd = fmaf(nq, dq[f], fmaf(nu, du[f], dnd));
+  }
+  Chol3 c;
+  if (!chol3(m00, m01, m02, m11, m12, m22, c)) return false;
+  float sq0, sq1, sq2, su0, su1, su2;
+  chol3_solve(c, bq0, bq1, bq2, sq0, sq1, sq2);
+  chol3_solve(c, bu0, bu1, bu2, su0, su1, su2);
+  float chi2 = 0.f, gbd = 0.f, gtd = 0.f, gbs = 0.f, hbd = 0.f, htd = 0.f, hbs = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    const float rq = dq[f] - fmaf(as[f], sq2, fmaf(ad[f], sq1, sq0));
+    const float ru = du[f] - fmaf(as[f], su2, fmaf(ad[f], su1, su0));
+    const float nrq = nn[f] * rq, nru = nn[f] * ru;
+    chi2 = fmaf(nrq, rq, fmaf(nru, ru, chi2));
+    if (GRAD) {
+      const float td = fmaf(nrq, sq1, nru * su1) * ad[f];
+      const float ts = fmaf(nrq, sq2, nru * su2) * as[f];
+      gbd = fmaf(td, bc.lnd[f], gbd);
+      gtd = fmaf(td, dt[f], gtd);
+      gbs = fmaf(ts, bc.lns[f], gbs);
+    }
+    if (HESS) {
+      const float a1 = ad[f] * ad[f] * nn[f], a2 = as[f] * as[f] * nn[f];
+      hbd = fmaf(a1 * bc.lnd[f], bc.lnd[f], hbd);
+      htd = fmaf(a1 * dt[f], dt[f], htd);
+      hbs = fmaf(a2 * bc.lns[f], bc.lns[f], hbs);
+    }
+  }
+  o.chi2 = chi2;
+  o.dnd = dnd;
+  o.gbd = -2.f * gbd;
+  o.gtd = -2.f * gtd;
+  o.gbs = -2.f * gbs;
+  if (HESS) {
+    const float k1 = 2.f * fmaf(sq1, sq1, su1 * su1), k2 = 2.f * fmaf(sq2, sq2, su2 * su2);
+    o.hbd = k1 * hbd;
+    o.htd = k1 * htd;
+    o.hbs = k2 * hbs;
+  }
+  return true;
+}
+
+// Load one pixel's Q and U vectors (one 128-byte line).
+__device__ __forceinline__ void load_pixel(const float* __restrict__ p, float (&dq)[NB],
+                                           float (&du)[NB]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 a = __ldg(p4 + k);
+    const float4 b = __ldg(p4 + 4 + k);
+    dq[4 * k + 0] = a.x; dq[4 * k + 1] = a.y; dq[4 * k + 2] = a.z; dq[4 * k + 3] = a.w;
+    du[4 * k + 0] = b.x; du[4 * k + 1] = b.y; du[4 * k + 2] = b.z; du[4 * k + 3] = b.w;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block reductions: every thread of the block receives the total. `sbuf` holds NT/32 values.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_sum(T v, T* sbuf) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = ((threadIdx.x & 31) < NT / 32) ? sbuf[threadIdx.x & 31] : T(0);
+  return warp_sum(t);
+}
+
+// Two sums at once (one pair of barriers).
+template <int NT, typename T>
+__device__ __forceinline__ void block_sum2(T& a, T& b, T* sbuf) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sbuf[threadIdx.x >> 5] = a;
+    sbuf[NT / 32 + (threadIdx.x >> 5)] = b;
+  }
+  __syncthreads();
+  const int l = threadIdx.x & 31;
+  T ta = (l < NT / 32) ? sbuf[l] : T(0);
+  T tb = (l < NT / 32) ? sbuf[NT / 32 + l] : T(0);
+  a = warp_sum(ta);
+  b = warp_sum(tb);
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_max(T v, T* sbuf) {
+  v = warp_max(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = ((threadIdx.x & 31) < NT / 32) ? sbuf[threadIdx.x & 31] : sbuf[0];
+  return warp_max(t);
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_min(T v, T* sbuf) {
+  v = warp_min(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = ((threadIdx.x & 31) < NT / 32) ? sbuf[threadIdx.x & 31] : sbuf[0];
+  return warp_min(t);
+}
+
+}  // namespace csx

@@ -1,0 +1,122 @@
+// Host-side internals of the csx library: error state, per-device scratch, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "csx_device.cuh"
+
+namespace csx {
+
+// ---- error reporting (thread-local message, negative return codes) ----------------------------
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+#define CSX_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// ---- per-device scratch: named grow-only buffers ----------------------------------------------
+enum ScratchId {
+  SCR_TABLES = 0,   // SED tables of csx_spectral_* / csx_reconstruct
+  SCR_FIT_SLOTS,    // per-CTA-slot state of the persistent fit
+  SCR_FIT_DESC,     // problem descriptors and queue order of the fit
+  SCR_CELLS,        // cell structure of the fit (perm, offsets, counts)
+  SCR_MISC,         // small counters
+  SCR_RECON_DESC,
+  SCR_COUNT
+};
+void* scratch(ScratchId id, size_t bytes, int* err);
+void scratch_release_all();
+
+Bands make_bands(const csx_model& m);
+
+// ---- problem descriptor of the fit / reconstruction ---------------------------------------------
+struct ProbDesc {
+  int conf, real;
+  int Kd, KT, Ks, P;
+  long long poff;   // offset of the problem's parameters in the packed arrays
+  long long toff;   // offset (in rows of 16 floats) of the problem's SED tables (reconstruction)
+};
+
+// ---- launchers (defined in the kernel translation units) -------------------------------------
+struct SpecArgs {
+  Bands bands;
+  int npix, nprob, Kd, KT, Ks, P, rows;
+  int noise_kind;
+  const float* d;
+  const float* w;
+  const float* ninv_pix;
+  float ninv_band[NB];
+  const int* labels;
+  const float* beta;
+  const float* tables;   // [nprob][rows][16]
+  double* L;
+  float* grad;
+};
+int launch_tables(const Bands& b, int nprob, int Kd, int KT, int Ks, const float* beta,
+                  float* tables, cudaStream_t s);
+int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA, cudaStream_t s);
+int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s);
+
+int launch_cells(int npix, int nconf, const int* labels, const int* K_dev, int* perm,
+                 int* cell_off, int* ncell, cudaStream_t s);
+
+struct FitArgs {
+  Bands bands;
+  int npix, nreal, noise_kind;
+  const float* d;
+  const float* w;
+  const float* ninv_pix;
+  float ninv_band[NB];
+  const int* labels;       // [nconf][3][npix]
+  const int* perm;         // [nconf][npix]
+  const int* cell_off;     // [nconf][npix+1]
+  const int* ncell;        // [nconf]
+  const ProbDesc* probs;   // [nprob]
+  const int* order;        // [nprob] queue order
+  int nprob;
+  int* head;               // queue head counter (zeroed by the launcher)
+  const float* beta0;
+  float* beta_out;
+  double* L_out;
+  int* status;
+  int* iters;
+  float* slots;            // per-slot scratch
+  long long slot_floats;
+  int Pmax, rows_max, ncell_max;
+  int history, max_iter, max_ls;
+  int path, grad_mode;
+  float lower[3], upper[3], xtol[3], fd_step;
+};
+int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s);
+int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path,
+                    long long* out);
+int fit_grid(int threads, int path, int grad_mode, int* grid);
+
+struct ReconArgs {
+  Bands bands;
+  int npix, nreal, noise_kind, nprob;
+  const float* d;
+  const float* w;
+  const float* ninv_pix;
+  float ninv_band[NB];
+  const int* labels;      // [nconf][3][npix]
+  const ProbDesc* probs;
+  const float* tables;    // rows per problem at probs[q].toff
+  const float* d_fg;
+  float* s_hat;
+  float* sigma2;
+  float* r_sys;
+  double* metrics;
+};
+int launch_recon_tables(const Bands& b, int nprob, const ProbDesc* probs, const float* beta,
+                        float* tables, long long total_rows, cudaStream_t s);
+int launch_recon(const ReconArgs& a, cudaStream_t s);
+int launch_select(int nconf, int nreal, const double* metrics, double* vtot, int* best,
+                  cudaStream_t s);
+
+}  // namespace csx

@@ -1,0 +1,304 @@
+"""ctypes binding of libcsx (include/csx.h). Argument marshalling only: every step of the method
+runs in the CUDA library. Device buffers are torch CUDA tensors; work is enqueued on torch's
+current CUDA stream. There is no CPU fallback: a missing library raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int32, c_void_p
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcsx.so")
+
+NB = 16
+NMETRIC = 8
+NOISE = {"homogeneous": 0, "separable": 1, "perpixel": 2}
+PATH = {"auto": 0, "stream": 1, "moment": 2}
+GRAD = {"adjoint": 0, "fd": 1}
+STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search"}
+M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
+
+EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
+           "csx_spectral_like", "csx_spectral_grad", "csx_build_cells", "csx_fit_batch",
+           "csx_reconstruct", "csx_select"]
+
+
+class CsxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("csx error %d: %s" % (code, msg))
+        self.code = code
+
+
+class CModel(ctypes.Structure):
+    _fields_ = [("nfreq", c_int32), ("units", c_int32), ("nu_ghz", c_double * NB),
+                ("nu0_dust_ghz", c_double), ("nu0_sync_ghz", c_double), ("t_cmb", c_double)]
+
+
+class CSky(ctypes.Structure):
+    _fields_ = [("npix", c_int32), ("nreal", c_int32), ("noise_kind", c_int32),
+                ("reserved", c_int32), ("d", c_void_p), ("ninv_band", c_float * NB),
+                ("w", c_void_p), ("ninv_pix", c_void_p)]
+
+
+class CFitOpts(ctypes.Structure):
+    _fields_ = [("max_iter", c_int32), ("history", c_int32), ("max_ls", c_int32),
+                ("path", c_int32), ("grad_mode", c_int32), ("threads", c_int32),
+                ("lower", c_float * 3), ("upper", c_float * 3), ("xtol", c_float * 3),
+                ("fd_step", c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcsx.so (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libcsx.so not built (run paper_2604_08463_b300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, pi32 = c_void_p, c_int32, POINTER(c_int32)
+        L.csx_version.restype = ctypes.c_char_p
+        L.csx_last_error.restype = ctypes.c_char_p
+        L.csx_release.restype = i32
+        L.csx_fit_defaults.argtypes = [POINTER(CFitOpts)]
+        L.csx_mixing.argtypes = [POINTER(CModel), i32, vp, vp, vp, vp]
+        L.csx_spectral_like.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp]
+        L.csx_spectral_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp, vp]
+        L.csx_build_cells.argtypes = [i32, i32, vp, pi32, vp, vp, vp, vp]
+        L.csx_fit_batch.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32,
+                                    POINTER(CFitOpts), vp, vp, vp, vp, vp, vp]
+        L.csx_reconstruct.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32, vp, vp, vp,
+                                      vp, vp, vp, vp]
+        L.csx_select.argtypes = [i32, i32, vp, vp, vp, vp]
+        for name in EXPORTS:
+            if name not in ("csx_version", "csx_last_error"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise CsxError(rc, lib().csx_last_error().decode())
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return c_void_p(t.data_ptr())
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+    return a, a.ctypes.data_as(POINTER(c_int32))
+
+
+class Model:
+    """Spectral model of Eq. 5: band centres (GHz), reference frequencies, units."""
+
+    def __init__(self, nu_ghz, nu0_dust=353.0, nu0_sync=23.0, t_cmb=2.7255, units="K_CMB"):
+        nu = np.asarray(nu_ghz, dtype=np.float64)
+        self.c = CModel()
+        self.c.nfreq = nu.size
+        self.c.units = 0 if units == "K_CMB" else 1
+        for f in range(nu.size):
+            self.c.nu_ghz[f] = nu[f]
+        self.c.nu0_dust_ghz = nu0_dust
+        self.c.nu0_sync_ghz = nu0_sync
+        self.c.t_cmb = t_cmb
+        self.nfreq = nu.size
+
+
+class Sky:
+    """Device-resident data and noise (Eq. 1).
+
+    d: float32 [nreal, npix, 2, 16] CUDA tensor; noise "homogeneous" (ninv_band),
+    "separable" (ninv_band, w [npix]) or "perpixel" (ninv_pix [npix, 16])."""
+
+    def __init__(self, d, noise="homogeneous", ninv_band=None, w=None, ninv_pix=None):
+        assert d.dtype == torch.float32 and d.dim() == 4 and d.shape[2] == 2 and d.shape[3] == NB
+        self.d = d.contiguous()
+        self.w = None if w is None else w.to(torch.float32).contiguous()
+        self.ninv_pix = None if ninv_pix is None else ninv_pix.to(torch.float32).contiguous()
+        self.noise = noise
+        self.c = CSky()
+        self.c.npix = d.shape[1]
+        self.c.nreal = d.shape[0]
+        self.c.noise_kind = NOISE[noise]
+        self.c.d = self.d.data_ptr() if d.numel() else None
+        if ninv_band is not None:
+            nb = np.asarray(ninv_band, dtype=np.float32)
+            for f in range(nb.size):
+                self.c.ninv_band[f] = float(nb[f])
+        self.c.w = self.w.data_ptr() if self.w is not None and self.w.numel() else None
+        self.c.ninv_pix = (self.ninv_pix.data_ptr() if self.ninv_pix is not None and
+                           self.ninv_pix.numel() else None)
+
+    @property
+    def npix(self):
+        return self.c.npix
+
+    @property
+    def nreal(self):
+        return self.c.nreal
+
+    def subset(self, nreal):
+        """A view on the first nreal realizations."""
+        s = Sky.__new__(Sky)
+        s.__dict__.update(self.__dict__)
+        s.c = CSky.from_buffer_copy(self.c)
+        s.c.nreal = nreal
+        return s
+
+
+def version():
+    return lib().csx_version().decode()
+
+
+def release():
+    _check(lib().csx_release())
+
+
+def mixing(model: Model, beta: torch.Tensor, want_derivatives=True):
+    """A [n, 16, 3] and dA [n, 3, 16] for beta [n, 3] = (beta_d, T_d, beta_s)."""
+    beta = beta.to(torch.float32).contiguous()
+    n = beta.shape[0]
+    A = torch.empty((n, NB, 3), device=beta.device, dtype=torch.float32)
+    dA = torch.empty((n, 3, NB), device=beta.device, dtype=torch.float32) if want_derivatives else None
+    _check(lib().csx_mixing(ctypes.byref(model.c), n, _ptr(beta), _ptr(A), _ptr(dA), _stream()))
+    return A, dA
+
+
+def spectral_like(model: Model, sky: Sky, labels, K, beta):
+    """L [nprob] (float64) for one configuration; beta [nprob, P], problem i uses realization i."""
+    K, Kp = _host_i32(K)
+    beta = beta.to(torch.float32).contiguous()
+    L = torch.empty(beta.shape[0], device=beta.device, dtype=torch.float64)
+    _check(lib().csx_spectral_like(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
+                                   beta.shape[0], _ptr(beta), _ptr(L), _stream()))
+    return L
+
+
+def spectral_grad(model: Model, sky: Sky, labels, K, beta):
+    """(L [nprob] float64, grad [nprob, P] float32)."""
+    K, Kp = _host_i32(K)
+    beta = beta.to(torch.float32).contiguous()
+    L = torch.empty(beta.shape[0], device=beta.device, dtype=torch.float64)
+    g = torch.empty_like(beta)
+    _check(lib().csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
+                                   beta.shape[0], _ptr(beta), _ptr(L), _ptr(g), _stream()))
+    return L, g
+
+
+def build_cells(labels: torch.Tensor, K):
+    """(perm [C, npix], cell_off [C, npix+1], ncell [C]) int32 for labels [C, 3, npix]."""
+    C, _, npix = labels.shape
+    K, Kp = _host_i32(K)
+    dev = labels.device
+    perm = torch.empty((C, npix), dtype=torch.int32, device=dev)
+    off = torch.empty((C, npix + 1), dtype=torch.int32, device=dev)
+    nc = torch.empty(C, dtype=torch.int32, device=dev)
+    _check(lib().csx_build_cells(npix, C, _ptr(labels), Kp, _ptr(perm), _ptr(off), _ptr(nc),
+                                 _stream()))
+    return perm, off, nc
+
+
+def fit_options(**kw) -> CFitOpts:
+    o = CFitOpts()
+    _check(lib().csx_fit_defaults(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "path":
+            v = PATH[v] if isinstance(v, str) else v
+        if k == "grad_mode":
+            v = GRAD[v] if isinstance(v, str) else v
+        if k in ("lower", "upper", "xtol"):
+            arr = getattr(o, k)
+            for j in range(3):
+                arr[j] = float(v[j])
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def param_offsets(K, nreal):
+    """Start of each problem's parameters in the packed layout (problem q = c * nreal + n)."""
+    K = np.asarray(K, dtype=np.int64)
+    P = K.sum(axis=1)
+    coff = np.concatenate([[0], np.cumsum(P)[:-1]])
+    q = []
+    for c in range(K.shape[0]):
+        for n in range(nreal):
+            q.append(nreal * coff[c] + n * P[c])
+    return np.array(q, dtype=np.int64), P
+
+
+def fit_batch(model: Model, sky: Sky, labels, K, beta0, **opts):
+    """Fit every (configuration, realization) problem. Returns dict of device tensors."""
+    K, Kp = _host_i32(K)
+    nconf = K.shape[0]
+    nprob = nconf * sky.nreal
+    dev = sky.d.device
+    beta0 = beta0.to(torch.float32).contiguous()
+    out = torch.empty_like(beta0)
+    L = torch.empty(nprob, dtype=torch.float64, device=dev)
+    st = torch.empty(nprob, dtype=torch.int32, device=dev)
+    it = torch.empty(nprob, dtype=torch.int32, device=dev)
+    o = fit_options(**opts)
+    _check(lib().csx_fit_batch(ctypes.byref(model.c), ctypes.byref(sky.c), nconf, _ptr(labels),
+                               Kp, ctypes.byref(o), _ptr(beta0), _ptr(out), _ptr(L), _ptr(st),
+                               _ptr(it), _stream()))
+    return {"beta": out, "L": L, "status": st, "iters": it}
+
+
+def reconstruct(model: Model, sky: Sky, labels, K, beta, d_fg=None, s_hat=False, sigma2=False,
+                r_sys=False, metrics=True):
+    """s_hat, sigma2, r_sys and per-problem metric sums at beta (packed per problem, the layout
+    of fit_batch: problem q = c * nreal + n)."""
+    K, Kp = _host_i32(K)
+    nprob = K.shape[0] * sky.nreal
+    dev = sky.d.device
+    npix = sky.npix
+    sh = torch.empty((nprob, npix, 2, 3), dtype=torch.float32, device=dev) if s_hat else None
+    sv = torch.empty((nprob, npix), dtype=torch.float32, device=dev) if sigma2 else None
+    rs = torch.empty((nprob, npix, 2), dtype=torch.float32, device=dev) if r_sys else None
+    me = torch.empty((nprob, NMETRIC), dtype=torch.float64, device=dev) if metrics else None
+    beta = beta.to(torch.float32).contiguous()
+    _check(lib().csx_reconstruct(ctypes.byref(model.c), ctypes.byref(sky.c), K.shape[0],
+                                 _ptr(labels), Kp, _ptr(beta), _ptr(d_fg), _ptr(sh), _ptr(sv),
+                                 _ptr(rs), _ptr(me), _stream()))
+    return {"s_hat": sh, "sigma2": sv, "r_sys": rs, "metrics": me}
+
+
+def select(metrics: torch.Tensor, nconf: int, nreal: int):
+    """(vtot [nconf] float64, best [1] int32) by total residual variance."""
+    v = torch.empty(nconf, dtype=torch.float64, device=metrics.device)
+    b = torch.empty(1, dtype=torch.int32, device=metrics.device)
+    _check(lib().csx_select(nconf, nreal, _ptr(metrics.contiguous()), _ptr(v), _ptr(b), _stream()))
+    return v, b
+
+
+class SpectralLikelihood(torch.autograd.Function):
+    """L(beta) for one configuration as a differentiable torch op (Sec. 3.3.1).
+
+    forward: csx_spectral_grad (one streaming pass gives L and dL/dbeta); only the gradient
+    [nprob, P] is saved, no per-pixel intermediate. backward: grad_output[:, None] * dL/dbeta."""
+
+    @staticmethod
+    def forward(ctx, beta, model, sky, labels, K):
+        L, g = spectral_grad(model, sky, labels, K, beta.detach())
+        ctx.save_for_backward(g)
+        return L
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return (grad_out.to(g.dtype)[:, None] * g).to(torch.float32), None, None, None, None

@@ -1,0 +1,71 @@
+"""The C ABI library (no GPU needed): it loads, exports every symbol include/csx.h declares, and
+the binding's ctypes structures have the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "csx.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(csx_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_08463_b300 import build, csx
+    build.build()
+    return csx.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2604_08463_b300 import csx
+    names = declared_functions()
+    assert len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(csx.EXPORTS) == names
+    so = os.path.join(ROOT, "paper_2604_08463_b300", "libcsx.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True,
+                         check=True).stdout
+    for n in names:
+        assert re.search(r"\bT %s$" % n, out, re.M), n
+
+
+def test_struct_layouts_match_c(lib):
+    from paper_2604_08463_b300 import csx
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "csx.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(csx_model), sizeof(csx_sky), sizeof(csx_fit_opts),
+         offsetof(csx_sky, ninv_band), offsetof(csx_sky, w), offsetof(csx_fit_opts, fd_step));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as t:
+        c = os.path.join(t, "s.c")
+        open(c, "w").write(src)
+        exe = os.path.join(t, "s")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert vals == [ctypes.sizeof(csx.CModel), ctypes.sizeof(csx.CSky), ctypes.sizeof(csx.CFitOpts),
+                    csx.CSky.ninv_band.offset, csx.CSky.w.offset, csx.CFitOpts.fd_step.offset]
+
+
+def test_host_only_calls(lib):
+    from paper_2604_08463_b300 import csx
+    assert csx.version().startswith("csx")
+    o = csx.fit_options(max_iter=7, path="moment")
+    assert o.max_iter == 7 and o.path == 2 and o.history == 8
+    # argument errors are reported before touching a device
+    rc = lib.csx_mixing(None, 1, None, None, None, None)
+    assert rc == -1 and b"model" in lib.csx_last_error()
