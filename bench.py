@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the batched adjoint fit of the nside-64 patch-configuration scan on B300.
+
+One step = the whole hot path over one batch: cell building, the persistent fit of every
+(configuration x realization) problem (SED tables, pixel assembly, GLS solves, likelihood,
+adjoint gradient, L-BFGS), the W.d reconstruction with residual diagnostics, and the selection.
+
+Workload: nside 64, |b| > 20 deg (32512 pixels), 1000 K-means patch configurations with
+(K_bd, K_Td, K_bs) log-uniform in 1..500, 10 noise realizations shared by all configurations
+(10000 problems); seeded synthetic LiteBIRD-like skies (see synth/).
+
+  python bench.py [--gpus N --steps K --warmup W]      # CUDA path (one JSON line on rank 0)
+  python bench.py --impl reference                     # FP64 CPU oracle on a bounded sample
+Multi-GPU (torchrun): rank r fits its own 1000 configurations (seed 4 + r): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "config fits/s & cluster-pixel L+grad L evals/s at nside64 vs plain form; % HBM peak"
+SCAN = dict(nside=64, nconf=1000, kmax=500, nreal=10, b_cut_deg=20.0)
+BYTES_PER_PIXEL_EVAL = 120 + 12 + 4   # 15 bands x Q,U float32 + 3 int32 labels + hit weight
+BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12  # residual moments (R, C, Q) + cell labels
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- inputs --------
+def make_inputs(rank: int, nconf: int):
+    import numpy as np
+    from synth import workloads
+    wl = workloads.scan(nside=SCAN["nside"], nconf=nconf, kmax=SCAN["kmax"], nreal=SCAN["nreal"],
+                        b_cut_deg=SCAN["b_cut_deg"], seed=4 + rank)
+    F = wl.sky.nfreq
+    nb32 = np.zeros(16, np.float32)
+    nb32[:F] = wl.sky.ninv_band.astype(np.float32)
+    beta0 = np.concatenate([np.tile(wl.beta0(c), wl.nreal) for c in range(wl.nconf)]).astype(np.float32)
+    return dict(wl=wl, d32=wl.data(), nb32=nb32, w32=wl.sky.w.astype(np.float32),
+                fg32=wl.foreground_padded(), labels=np.ascontiguousarray(wl.labels, dtype=np.int32),
+                K=np.ascontiguousarray(wl.K, dtype=np.int32), beta0=beta0)
+
+
+# ----------------------------------------------------------------------------- clocks --------
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle --------
+def _oracle_job(args):
+    import numpy as np
+    from oracle import fit as ofit
+    nu, d64, ninv64, lab, K, beta0, lower, upper = args
+    t = time.time()
+    x, L, info = ofit.fit(nu, d64, ninv64, lab, K, beta0, lower, upper, polish=False)
+    return time.time() - t, int(info["nit"])
+
+
+def oracle_sample(inp, budget_s: float = 20.0):
+    """Fit a bounded, seeded sample of problems with the FP64 oracle on the host cores."""
+    import multiprocessing as mp
+    import numpy as np
+    from synth import workloads
+    wl = inp["wl"]
+    cores = len(os.sched_getaffinity(0))
+    P = wl.P
+    # problems with parameter counts near the scan's median, realization 0
+    order = np.argsort(np.abs(P - np.median(P)), kind="stable")
+    nsample = max(1, min(cores, 16))
+    F = wl.sky.nfreq
+    ninv64 = inp["w32"].astype(np.float64)[:, None] * inp["nb32"][:F].astype(np.float64)
+    d64 = inp["d32"][0, :, :, :F].astype(np.float64)
+    jobs = [(wl.sky.nu, d64, ninv64, wl.labels[c], wl.K[c], wl.beta0(c), workloads.LOWER,
+             workloads.UPPER) for c in order[:nsample]]
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    # one problem per worker, all started together: about one oracle fit time (~20-40 s) of wall
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(cores, nsample)) as pool:
+        done = list(pool.imap_unordered(_oracle_job, jobs))
+    wall = time.time() - t0
+    n = len(done)
+    return {"value": n / wall, "unit": "fits/s", "cores": min(cores, nsample), "kind": "oracle",
+            "sample": "%d of %d problems (P near the scan median %d, realization 0), nside 64, "
+                      "32512 pixels, FP64 numpy/scipy L-BFGS-B, one process per core"
+                      % (n, wl.nconf * wl.nreal, int(np.median(P))),
+            "single_fit_s_mean": float(np.mean([d[0] for d in done])),
+            "oracle_iters_mean": float(np.mean([d[1] for d in done]))}
+
+
+# ----------------------------------------------------------------------------- CUDA arm -------
+def run_csx(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2604_08463_b300 import csx
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    inp = make_inputs(rank, args.nconf)
+    cpu_base = oracle_sample(inp) if (rank == 0 and world == 1 and not args.no_cpu) else None
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    wl = inp["wl"]
+    nconf, nreal, npix = wl.nconf, wl.nreal, wl.npix
+    nprob = nconf * nreal
+    dev = torch.device("cuda", local)
+    d = torch.from_numpy(inp["d32"]).to(dev)
+    w = torch.from_numpy(inp["w32"]).to(dev)
+    fg = torch.from_numpy(inp["fg32"]).to(dev)
+    labels = torch.from_numpy(inp["labels"]).to(dev)
+    beta0 = torch.from_numpy(inp["beta0"]).to(dev)
+    K = inp["K"]
+    model = csx.Model(wl.sky.nu)
+    sky = csx.Sky(d, noise="separable", ninv_band=inp["nb32"], w=w)
+    opts = dict(path=args.path)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        res = csx.fit_batch(model, sky, labels, K, beta0, **opts)
+        rec = csx.reconstruct(model, sky, labels, K, res["beta"], d_fg=fg, metrics=True)
+        vt, best = csx.select(rec["metrics"], nconf, nreal)
+        return res, rec, vt, best
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    fit_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    evals = []
+    e0.record(stream)
+    for k in range(args.steps):
+        flush.zero_()
+        fit_ev[k][0].record(stream)
+        res = csx.fit_batch(model, sky, labels, K, beta0, **opts)
+        fit_ev[k][1].record(stream)
+        rec = csx.reconstruct(model, sky, labels, K, res["beta"], d_fg=fg, metrics=True)
+        vt, best = csx.select(rec["metrics"], nconf, nreal)
+        evals.append(res["nevals"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    fit_ms = statistics.mean(a.elapsed_time(b) for a, b in fit_ev)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+
+    status = res["status"].cpu().numpy()
+    iters = res["iters"].cpu().numpy()
+    nev = torch.stack(evals).to(torch.float64).mean(0).cpu().numpy()
+    path = "moment" if args.path == "moment" else "stream"
+    units_per_eval = npix if path == "stream" else None
+    if path == "stream":
+        unit_evals = float(nev.sum()) * npix
+        alg_bytes = unit_evals * BYTES_PER_PIXEL_EVAL
+    else:
+        unit_evals = float(nev.sum())  # refined below by cell counts
+        alg_bytes = unit_evals * BYTES_PER_CELL_EVAL
+    hbm, peak_kind = peaks()
+    achieved = alg_bytes / (fit_ms * 1e-3) / 1e9
+
+    # end to end: pinned host inputs -> device, step, results -> host
+    e2e = None
+    if args.e2e_steps > 0:
+        h_d = torch.from_numpy(inp["d32"]).pin_memory()
+        h_w = torch.from_numpy(inp["w32"]).pin_memory()
+        h_fg = torch.from_numpy(inp["fg32"]).pin_memory()
+        h_lab = torch.from_numpy(inp["labels"]).pin_memory()
+        h_b0 = torch.from_numpy(inp["beta0"]).pin_memory()
+        out_b = torch.empty(beta0.shape, dtype=torch.float32).pin_memory()
+        out_L = torch.empty(nprob, dtype=torch.float64).pin_memory()
+        out_s = torch.empty(nprob, dtype=torch.int32).pin_memory()
+        out_v = torch.empty(nconf, dtype=torch.float64).pin_memory()
+        out_best = torch.empty(1, dtype=torch.int32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in (h_d, h_w, h_fg, h_lab, h_b0))
+        d2h = sum(t.numel() * t.element_size() for t in (out_b, out_L, out_s, out_v, out_best))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.e2e_steps):
+            flush.zero_()
+            d.copy_(h_d, non_blocking=True)
+            w.copy_(h_w, non_blocking=True)
+            fg.copy_(h_fg, non_blocking=True)
+            labels.copy_(h_lab, non_blocking=True)
+            beta0.copy_(h_b0, non_blocking=True)
+            r2, _, v2, b2 = step()
+            out_b.copy_(r2["beta"], non_blocking=True)
+            out_L.copy_(r2["L"], non_blocking=True)
+            out_s.copy_(r2["status"], non_blocking=True)
+            out_v.copy_(v2, non_blocking=True)
+            out_best.copy_(b2, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = s0.elapsed_time(s1) / args.e2e_steps
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * nprob / (e2e_ms * 1e-3), "unit": "fits/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms}
+
+    plain = None
+    if rank == 0 and not args.no_plain:
+        plain = plain_form(csx, model, sky, labels, inp, fit_ms / max(1.0, float(iters.mean())),
+                           float(iters.mean()), nprob / (ms * 1e-3))
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    launches_per_step = 4 + (1 if path == "moment" else 0)
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC,
+        "value": world * nprob / (ms_max * 1e-3),
+        "unit": "fits/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (FP32 pixel arithmetic, FP64 sums)",
+        "data": "synthetic (seeded LiteBIRD-like skies, K-means patches)",
+        "config": {"workload": wl.name, "nside": SCAN["nside"], "npix": npix, "nconf": nconf,
+                   "nreal": nreal, "problems_per_gpu": nprob, "mean_P": float(wl.P.mean()),
+                   "max_P": int(wl.P.max()), "fit_path": path,
+                   "l2": "256 MiB buffer written before every timed step (L2 is 126 MB)",
+                   "parallelism": "weak: each rank fits its own 1000 configurations"},
+        "pixel_evals_per_s": (float(nev.sum()) * npix / (fit_ms * 1e-3)) if path == "stream" else None,
+        "fit_ms": fit_ms,
+        "fit_stats": {"converged": int((status == 0).sum()), "max_iter": int((status == 1).sum()),
+                      "line_search": int((status == 3).sum()), "nonphysical": int((status == 2).sum()),
+                      "iters_mean": float(iters.mean()), "evals_mean": float(nev.mean())},
+        "roofline": {"kernel": "k_fit (persistent fit)", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "bytes_per_unit": BYTES_PER_PIXEL_EVAL if path == "stream" else BYTES_PER_CELL_EVAL,
+                     "traffic": None,
+                     "note": "algorithmic bytes of every likelihood evaluation / fit-kernel time; the "
+                             "10 realizations' data (42 MB) stay resident in L2, so this can exceed DRAM"},
+        "cpu_baseline": cpu_base,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "plain_form": plain,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fits_per_s):
+    """Plain GPU form: the same optimiser with central finite-difference gradients of the forward
+    likelihood (2P+1 evaluations per gradient), on 20 configurations spanning the P range."""
+    import numpy as np
+    import torch
+    wl = inp["wl"]
+    P = wl.P
+    qs = np.quantile(P, np.linspace(0.0, 1.0, 20))
+    pick = sorted({int(np.argmin(np.abs(P - q))) for q in qs})
+    sub_lab = labels[pick].contiguous()
+    K = inp["K"][pick]
+    b0 = torch.tensor(np.concatenate([np.tile(wl.beta0(c), wl.nreal) for c in pick]),
+                      dtype=torch.float32, device=labels.device)
+    max_iter = 10
+    torch.cuda.synchronize()
+    t0 = time.time()
+    res = csx.fit_batch(model, sky, sub_lab, K, b0, grad_mode="fd", path="stream", max_iter=max_iter)
+    torch.cuda.synchronize()
+    wall = time.time() - t0
+    it = res["iters"].cpu().numpy()
+    ne = res["nevals"].cpu().numpy()
+    # time per quasi-Newton iteration of the plain form, scaled to the adjoint fit's iteration count
+    nprob = len(pick) * wl.nreal
+    per_iter = wall / max(1.0, float(it.mean()))
+    extrap_fit_s = per_iter * adj_iters
+    fits_per_s = nprob / extrap_fit_s
+    return {"subset": "%d configurations (P quantiles %d..%d) x %d realizations, max_iter %d"
+                      % (len(pick), int(P[pick].min()), int(P[pick].max()), wl.nreal, max_iter),
+            "wall_s": wall, "iters_mean": float(it.mean()), "evals_mean": float(ne.mean()),
+            "fits_per_s_extrapolated": fits_per_s,
+            "extrapolation": "subset wall time per iteration x the adjoint fit's mean iterations "
+                             "(%.1f); the subset's P mix differs from the full scan" % adj_iters,
+            "adjoint_speedup": adj_fits_per_s / fits_per_s}
+
+
+# ----------------------------------------------------------------------------- reference ------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inp = make_inputs(0, args.nconf)
+    vals = []
+    last = None
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    t0 = time.time()
+    for _ in range(args.steps):
+        last = oracle_sample(inp, budget_s=args.ref_budget)
+        vals.append(last["value"])
+    wall = time.time() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "fits/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded LiteBIRD-like skies, K-means patches)",
+            "config": {"workload": inp["wl"].name, "npix": inp["wl"].npix,
+                       "note": "each step fits a bounded sample of the scan's problems on the host"},
+            "cpu_baseline": dict(last, value=v),
+            "e2e": {"value": v, "unit": "fits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["csx", "reference"], default="csx")
+    ap.add_argument("--path", choices=["auto", "stream", "moment"], default="auto")
+    ap.add_argument("--nconf", type=int, default=SCAN["nconf"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_csx(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -176,13 +176,16 @@ int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const in
  *   beta0, beta_out  device float, packed per problem: problem q starts at
  *           nreal * coff[c] + n * P_c with coff[c] = sum_{c' < c} P_c' (beta_out may alias beta0)
  *   L_out   device double [nconf * nreal] (L at beta_out), status / iters device int32 [nconf*nreal]
+ *   nevals  device int32 [nconf * nreal] or NULL: likelihood evaluations performed per problem
+ *           (each forward evaluation of a finite-difference gradient counts once)
  * Optimiser: L-BFGS in Gauss-Newton-scaled variables with the active-set bound handling and
  * step limit of App. A, line search on approximate Wolfe conditions. With the moment path the call
  * synchronises `stream` once (to read the cell counts).
  */
 int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
                   const int32_t* K, const csx_fit_opts* opts, const float* beta0, float* beta_out,
-                  double* L_out, int32_t* status, int32_t* iters, void* stream);
+                  double* L_out, int32_t* status, int32_t* iters, int32_t* nevals,
+                  void* stream);
 
 /*
  * Reconstruction s_hat = W d, W = (A^T N^-1 A)^-1 A^T N^-1 (Eqs. 3, 8) and residual diagnostics

@@ -104,6 +104,29 @@ def spectral_gradient(nu, d, ninv, labels, K, beta):
     return L, grad
 
 
+def gradient_term_scale(nu, d, ninv, labels, K, beta, data_scale=False):
+    """S_theta = 2 sum over the pixels of theta's patch, the Stokes parameters and the bands of
+    |w_r (dA/dtheta) s_hat| : the summed magnitude of the terms whose signed sum is dL/dtheta.
+    A finite-precision evaluation of dL/dtheta carries an error proportional to S_theta, however
+    small the signed sum is.
+
+    data_scale=True replaces |w_r| = |N^-1 (d - A s_hat)| by |N^-1 d|: the scale of the rounding
+    made when the residual d - A s_hat is formed in finite precision (relative error u |d| / |r|)."""
+    kd, kt, ks = (int(k) for k in K)
+    bd, td, bs = pixel_parameters(beta, labels, K)
+    A = mixing_matrix(nu, bd, td, bs)
+    dbd, dtd, dbs = mixing_derivatives(nu, bd, td, bs)
+    M, b = normal_equations(A, ninv, d)
+    s = np.linalg.solve(M[:, None, :, :], b[..., None])[..., 0]
+    wr = ninv[:, None, :] * (d if data_scale else d - np.einsum("pfi,psi->psf", A, s))
+    t_bd = 2.0 * np.abs(np.einsum("psf,pf,ps->psf", wr, dbd, s[:, :, 1])).sum(axis=(1, 2))
+    t_td = 2.0 * np.abs(np.einsum("psf,pf,ps->psf", wr, dtd, s[:, :, 1])).sum(axis=(1, 2))
+    t_bs = 2.0 * np.abs(np.einsum("psf,pf,ps->psf", wr, dbs, s[:, :, 2])).sum(axis=(1, 2))
+    return np.concatenate([np.bincount(labels[0], weights=t_bd, minlength=kd),
+                           np.bincount(labels[1], weights=t_td, minlength=kt),
+                           np.bincount(labels[2], weights=t_bs, minlength=ks)])
+
+
 def ninv_from(ninv_band, w, npix):
     """Per-pixel diagonal N^-1 [npix, F] from per-band 1/sigma^2 and per-pixel weights (None = 1)."""
     ninv_band = np.asarray(ninv_band, dtype=np.float64)

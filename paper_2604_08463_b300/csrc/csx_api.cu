@@ -274,7 +274,8 @@ int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const in
 
 int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
                   const int32_t* K, const csx_fit_opts* opts, const float* beta0, float* beta_out,
-                  double* L_out, int32_t* status, int32_t* iters, void* stream) {
+                  double* L_out, int32_t* status, int32_t* iters, int32_t* nevals,
+                  void* stream) {
   int rc = check_model(m);
   if (rc) return rc;
   if ((rc = check_sky(sky, m->nfreq))) return rc;
@@ -296,9 +297,7 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   if (o.lower[1] <= 0.f) return fail(CSX_EINVAL, "T_d lower bound must be > 0");
   if (o.grad_mode == CSX_GRAD_FD && !(o.fd_step > 0)) return fail(CSX_EINVAL, "fd_step must be > 0");
   int path = o.path;
-  if (path == CSX_PATH_AUTO)
-    path = (sky->noise_kind != CSX_NOISE_PERPIXEL && o.grad_mode == CSX_GRAD_ADJOINT) ? CSX_PATH_MOMENT
-                                                                                     : CSX_PATH_STREAM;
+  if (path == CSX_PATH_AUTO) path = CSX_PATH_STREAM;
   if (path != CSX_PATH_MOMENT && path != CSX_PATH_STREAM) return fail(CSX_EINVAL, "unknown path");
   if (path == CSX_PATH_MOMENT && sky->noise_kind == CSX_NOISE_PERPIXEL)
     return fail(CSX_EINVAL, "the moment path needs homogeneous or separable noise");
@@ -403,6 +402,7 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   a.L_out = L_out;
   a.status = status;
   a.iters = iters;
+  a.nevals = nevals;
   a.slots = slots;
   a.slot_floats = slot_floats;
   a.Pmax = Pmax;

@@ -110,7 +110,7 @@ __device__ __forceinline__ void chol3_inverse(const Chol3& c, float& v00, float&
 
 // ---------------------------------------------------------------------------------------------
 // Per-pixel likelihood in the residual form and adjoint gradient contributions.
-//   M = A^T N A, b_s = A^T N d_s, s_hat = M^-1 b_s, r_s = d_s - A s_hat,
+//   s_hat = (A^T N A)^-1 A^T N d_s (Eq. 3), r_s = d_s - A s_hat,
 //   chi2 = sum_s r_s^T N r_s, dnd = sum_s d_s^T N d_s  (L_pixel = chi2 - dnd),
 //   dL/dtheta = -2 sum_s (N r_s)^T (dA/dtheta) s_hat_s   (Sec. 3.3.1)
 // with dA_d/dbeta_d = A_d ln(nu/nu0_d), dA_d/dT_d = A_d D, dA_s/dbeta_s = A_s ln(nu/nu0_s).
@@ -123,6 +123,59 @@ struct PixOut {
   float hbd, htd, hbs;
 };
 
+// The GLS solve uses modified Gram-Schmidt on the columns (1, A_d, A_s) in the N-weighted inner
+// product instead of the normal equations: the same result with rounding error growing with
+// cond(N^1/2 A) rather than its square cond(A^T N A).
+//   c1 = A_d - mu1,            mu1 = <1, A_d> / <1, 1>
+//   c2 = A_s - mu2 - nu c1,    mu2 = <1, A_s> / <1, 1>,  nu = <c1, A_s> / <c1, c1>
+//   t = (<1,d>/<1,1>, <c1,d>/<c1,c1>, <c2,d>/<c2,c2>),  r = d - t0 - t1 c1 - t2 c2,
+//   s_hat = (t0 - mu1 s1 - mu2 s2, t1 - nu t2, t2).
+struct Mgs3 {
+  float mu1, mu2, nu, i0, i1, i2;  // i_k = 1 / <c_k, c_k>
+};
+
+__device__ __forceinline__ bool mgs3(const float (&nn)[NB], const float (&ad)[NB],
+                                     const float (&as)[NB], float (&c1)[NB], float (&c2)[NB],
+                                     Mgs3& g) {
+  float n0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    n0 += nn[f];
+    s1 = fmaf(nn[f], ad[f], s1);
+    s2 = fmaf(nn[f], as[f], s2);
+  }
+  if (!(n0 > 0.f)) return false;
+  g.i0 = 1.f / n0;
+  g.mu1 = s1 * g.i0;
+  g.mu2 = s2 * g.i0;
+  float n1 = 0.f, x12 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    c1[f] = ad[f] - g.mu1;
+    const float w = nn[f] * c1[f];
+    n1 = fmaf(w, c1[f], n1);
+    x12 = fmaf(w, as[f], x12);
+  }
+  if (!(n1 > 0.f)) return false;
+  g.i1 = 1.f / n1;
+  g.nu = x12 * g.i1;
+  float n2 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    c2[f] = fmaf(-g.nu, c1[f], as[f] - g.mu2);
+    n2 = fmaf(nn[f] * c2[f], c2[f], n2);
+  }
+  if (!(n2 > 0.f)) return false;
+  g.i2 = 1.f / n2;
+  return true;
+}
+
+// [(A^T N A)^-1]_00 from the Gram-Schmidt factors.
+__device__ __forceinline__ float mgs3_var00(const Mgs3& g) {
+  const float r02 = g.mu1 * g.nu - g.mu2;
+  return g.i0 + g.mu1 * g.mu1 * g.i1 + r02 * r02 * g.i2;
+}
+
 template <bool GRAD, bool HESS>
 __device__ __forceinline__ bool pixel_eval(const float (&dq)[NB], const float (&du)[NB],
                                            const float (&nn)[NB], const float* __restrict__ pd,
@@ -130,10 +183,7 @@ __device__ __forceinline__ bool pixel_eval(const float (&dq)[NB], const float (&
                                            const float* __restrict__ dt,
                                            const float* __restrict__ ss, const Bands& bc,
                                            PixOut& o) {
-  float ad[NB], as[NB];
-  float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
-  float bq0 = 0.f, bq1 = 0.f, bq2 = 0.f, bu0 = 0.f, bu1 = 0.f, bu2 = 0.f;
-  float dnd = 0.f;
+  float ad[NB], as[NB], c1[NB], c2[NB];
 #pragma unroll
   for (int f4 = 0; f4 < NB; f4 += 4) {
     const float4 p4 = *reinterpret_cast<const float4*>(pd + f4);
@@ -143,35 +193,29 @@ __device__ __forceinline__ bool pixel_eval(const float (&dq)[NB], const float (&
     ad[f4 + 2] = p4.z * b4.z; ad[f4 + 3] = p4.w * b4.w;
     as[f4 + 0] = s4.x; as[f4 + 1] = s4.y; as[f4 + 2] = s4.z; as[f4 + 3] = s4.w;
   }
+  Mgs3 g;
+  if (!mgs3(nn, ad, as, c1, c2, g)) return false;
+  float tq0 = 0.f, tq1 = 0.f, tq2 = 0.f, tu0 = 0.f, tu1 = 0.f, tu2 = 0.f, dnd = 0.f;
 #pragma unroll
   for (int f = 0; f < NB; ++f) {
-    const float n = nn[f];
-    const float na1 = n * ad[f], na2 = n * as[f];
-    m00 += n;
-    m01 += na1;
-    m02 += na2;
-    m11 = fmaf(na1, ad[f], m11);
-    m12 = fmaf(na1, as[f], m12);
-    m22 = fmaf(na2, as[f], m22);
-    const float nq = n * dq[f], nu = n * du[f];
-    bq0 += nq;
-    bq1 = fmaf(na1, dq[f], bq1);
-    bq2 = fmaf(na2, dq[f], bq2);
-    bu0 += nu;
-    bu1 = fmaf(na1, du[f], bu1);
-    bu2 = fmaf(na2, du[f], bu2);
+    const float nq = nn[f] * dq[f], nu = nn[f] * du[f];
+    tq0 += nq;
+    tq1 = fmaf(nq, c1[f], tq1);
+    tq2 = fmaf(nq, c2[f], tq2);
+    tu0 += nu;
+    tu1 = fmaf(nu, c1[f], tu1);
+    tu2 = fmaf(nu, c2[f], tu2);
     dnd = fmaf(nq, dq[f], fmaf(nu, du[f], dnd));
   }
-  Chol3 c;
-  if (!chol3(m00, m01, m02, m11, m12, m22, c)) return false;
-  float sq0, sq1, sq2, su0, su1, su2;
-  chol3_solve(c, bq0, bq1, bq2, sq0, sq1, sq2);
-  chol3_solve(c, bu0, bu1, bu2, su0, su1, su2);
+  tq0 *= g.i0; tq1 *= g.i1; tq2 *= g.i2;
+  tu0 *= g.i0; tu1 *= g.i1; tu2 *= g.i2;
+  const float sq2 = tq2, sq1 = fmaf(-g.nu, tq2, tq1);
+  const float su2 = tu2, su1 = fmaf(-g.nu, tu2, tu1);
   float chi2 = 0.f, gbd = 0.f, gtd = 0.f, gbs = 0.f, hbd = 0.f, htd = 0.f, hbs = 0.f;
 #pragma unroll
   for (int f = 0; f < NB; ++f) {
-    const float rq = dq[f] - fmaf(as[f], sq2, fmaf(ad[f], sq1, sq0));
-    const float ru = du[f] - fmaf(as[f], su2, fmaf(ad[f], su1, su0));
+    const float rq = dq[f] - fmaf(tq2, c2[f], fmaf(tq1, c1[f], tq0));
+    const float ru = du[f] - fmaf(tu2, c2[f], fmaf(tu1, c1[f], tu0));
     const float nrq = nn[f] * rq, nru = nn[f] * ru;
     chi2 = fmaf(nrq, rq, fmaf(nru, ru, chi2));
     if (GRAD) {

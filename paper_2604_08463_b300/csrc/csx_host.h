@@ -85,6 +85,7 @@ struct FitArgs {
   double* L_out;
   int* status;
   int* iters;
+  int* nevals;             // may be NULL
   float* slots;            // per-slot scratch
   long long slot_floats;
   int Pmax, rows_max, ncell_max;

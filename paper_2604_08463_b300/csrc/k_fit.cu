@@ -4,10 +4,11 @@
 //
 //   likelihood + adjoint gradient (Eq. 4, Sec. 3.3.1), by one of two exact evaluations
 //     MOMENT: separable noise N_p^-1 = w_p diag(n): every pixel of a cell (equal (l_d,l_T,l_s))
-//             has the same A, so L = -sum_c tr[M_c^-1 A^T n S_c n A],  S_c = sum_{p in c} w_p
-//             sum_s d d^T is built once per problem (one pass over the pixels) and each evaluation
-//             costs O(cells), not O(pixels):
-//               dL/dA = -2 (n S n A - n A M^-1 G) M^-1,  G = A^T n S n A,  M = A^T n A.
+//             has the same A, so chi2 and its gradient need only the cell's weighted second
+//             moments, kept as residual moments about a reference point (see build_moments and
+//             eval_moment): one pass over the pixels per reference point, then each evaluation
+//             costs O(cells), not O(pixels). The reference point is moved to the current point
+//             (at most 3 times) when the fit converges far from it.
 //     STREAM: per pixel, residual form (any diagonal noise).
 //   the optimiser: L-BFGS (memory m) in variables scaled by the square root of the Gauss-Newton
 //     diagonal at the start point; box bounds handled as in App. A: parameters at a bound whose
@@ -35,7 +36,9 @@ struct Ctx {
   const int* coff;    // cell offsets
   const float* d;     // [npix][2][16] of the realization
   float *z, *g, *p, *zt, *gt, *hs, *x, *gacc, *hacc, *S, *Y, *tab, *mom;
+  float *tabr, *xr;   // moment path: SED tables and parameters of the reference point
   int* trip;
+  float* smem;        // moment path: dynamic shared memory (build staging, then per-thread rows)
 };
 
 struct Shared {
@@ -50,93 +53,180 @@ __device__ __forceinline__ int ptype(const Ctx& c, int i) {
 
 // ------------------------------------------------------------------------------ tables ----------
 template <int NT>
-__device__ void fill_tables(const FitArgs& a, Ctx& c) {
+__device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, float* tab) {
   const int n = c.rows * NB;
-  for (int i = threadIdx.x; i < n; i += NT) c.tab[i] = table_entry(a.bands, i >> 4, i & 15, c.Kd, c.KT, c.x);
+  for (int i = threadIdx.x; i < n; i += NT) tab[i] = table_entry(a.bands, i >> 4, i & 15, c.Kd, c.KT, x);
   __syncthreads();
 }
 
 // ------------------------------------------------------------------------------ moments ---------
-// S_c[e(i,j)] for i <= j < 15, e = i(29-i)/2 + j, stored entry-major: mom[e * ncell + cell].
-// One warp per cell; lanes 0..29 = 10 upper-triangle 4x4 blocks x 3 pixel groups; partial sums
-// are flushed to a second accumulator every 16 pixels to bound FP32 rounding growth.
+// Residual moments of a cell about a reference point beta_ref (tables c.tabr). Per pixel and Stokes,
+// with A_r the cell's mixing matrix at beta_ref:
+//   s = (A_r^T N A_r)^-1 A_r^T N d,   r = d - A_r s,   v = [r_0 .. r_14, s_0, s_1, s_2]
+// and per cell M_c = sum_p w_p sum_s v v^T (18 x 18): its blocks are R = sum w r r^T,
+// C = sum w r s^T and Q = sum w s s^T. Stored as the upper triangle, entry-major:
+//   mom[e(i,j) * ncell + cell],  e(i,j) = i (35 - i) / 2 + j,  0 <= i <= j < 18   (171 entries).
+// Since d = A_r s + r exactly, S_c = sum w d d^T = A_r Q A_r^T + A_r C^T + C A_r^T + R, but every stored
+// block is small where it has to be: R and C carry residuals, not the foreground signal.
+//
+// One warp per cell. Phase 1, lane = pixel: the cell's Gram-Schmidt basis of A_r (computed once per
+// cell, the noise weight w_p scales out of s and r), then s and r of up to 32 pixels into shared
+// memory. Phase 2: lanes = 15 upper 4x4 blocks of the 20x20 (zero-padded) v v^T x 2 pixel groups;
+// partial sums are flushed every 16 pixels to bound FP32 rounding growth. Also sum w d^T n d.
+constexpr int NM = 171;          // stored moment entries per cell
+constexpr int VROW = 44;         // shared floats per pixel: v_Q[20], v_U[20], w (16-byte rows)
+constexpr int BUILD_SMEM_PER_WARP = 32 * VROW;
+
+__device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
+
 template <int NT, bool SEP>
-__device__ void build_moments(const FitArgs& a, Ctx& c) {
+__device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane / 10, blk = lane % 10;
-  const int ba = blk < 4 ? 0 : (blk < 7 ? 1 : (blk < 9 ? 2 : 3));
-  const int bb = ba + blk - (ba == 0 ? 0 : (ba == 1 ? 4 : (ba == 2 ? 7 : 9)));
+  float* sv = smem + warp * BUILD_SMEM_PER_WARP;
+  const int grp = lane / 15, blk = lane % 15;
+  // upper-triangle 4x4 blocks of a 5x5 block grid: (ba, bb), ba <= bb
+  int ba = 0, rem = blk;
+  while (rem >= 5 - ba) {
+    rem -= 5 - ba;
+    ++ba;
+  }
+  const int bb = ba + rem;
+  const float* nb = a.ninv_band;
+  double dnd = 0.0;
   for (int cell = warp; cell < c.ncell; cell += NT / 32) {
     const int i0 = c.coff[cell], i1 = c.coff[cell + 1];
+    const int px0 = c.perm[i0];
+    const int kd = c.lab[px0], kt = c.lab[c.npix + px0], ks = c.lab[2 * c.npix + px0];
+    float ad[NB], as[NB], c1[NB], c2[NB], nn[NB];
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+      ad[f] = c.tabr[kd * NB + f] * c.tabr[(c.Kd + kt) * NB + f];
+      as[f] = c.tabr[(c.Kd + 2 * c.KT + ks) * NB + f];
+      nn[f] = nb[f];
+    }
+    Mgs3 g;
+    const bool okb = mgs3(nn, ad, as, c1, c2, g);
     float acc[16], tot[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = tot[k] = 0.f;
-    if (grp < 3) {
-      int cnt = 0;
-      for (int i = i0 + grp; i < i1; i += 3) {
+    int cnt = 0;
+    for (int base = i0; base < i1; base += 32) {
+      const int i = base + lane;
+      float* row = sv + lane * VROW;
+      if (i < i1) {
         const int px = c.perm[i];
         const float wp = SEP ? __ldg(a.w + px) : 1.f;
-        const float4* base = reinterpret_cast<const float4*>(c.d + (long long)px * 2 * NB);
-        float4 rq = __ldg(base + ba), cq = __ldg(base + bb);
-        float4 ru = __ldg(base + 4 + ba), cu = __ldg(base + 4 + bb);
-        const float r[8] = {rq.x * wp, rq.y * wp, rq.z * wp, rq.w * wp,
-                            ru.x * wp, ru.y * wp, ru.z * wp, ru.w * wp};
-        const float cc[8] = {cq.x, cq.y, cq.z, cq.w, cu.x, cu.y, cu.z, cu.w};
+        float dq[NB], du[NB];
+        load_pixel(c.d + (long long)px * 2 * NB, dq, du);
+        float tq0 = 0.f, tq1 = 0.f, tq2 = 0.f, tu0 = 0.f, tu1 = 0.f, tu2 = 0.f, pd = 0.f;
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii)
+        for (int f = 0; f < NB; ++f) {
+          const float nq = nb[f] * dq[f], nu = nb[f] * du[f];
+          tq0 += nq;
+          tq1 = fmaf(nq, c1[f], tq1);
+          tq2 = fmaf(nq, c2[f], tq2);
+          tu0 += nu;
+          tu1 = fmaf(nu, c1[f], tu1);
+          tu2 = fmaf(nu, c2[f], tu2);
+          pd = fmaf(nq, dq[f], fmaf(nu, du[f], pd));
+        }
+        dnd += (double)(wp * pd);
+        tq0 *= g.i0; tq1 *= g.i1; tq2 *= g.i2;
+        tu0 *= g.i0; tu1 *= g.i1; tu2 *= g.i2;
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj)
-            acc[ii * 4 + jj] = fmaf(r[ii], cc[jj], fmaf(r[4 + ii], cc[4 + jj], acc[ii * 4 + jj]));
-        if (++cnt == 16) {
+        for (int f = 0; f < NB; ++f) {
+          row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2[f], fmaf(tq1, c1[f], tq0)) : 0.f;
+          row[20 + f] = (f < 15) ? du[f] - fmaf(tu2, c2[f], fmaf(tu1, c1[f], tu0)) : 0.f;
+        }
+        // s = R^-1 t (Gram-Schmidt back-substitution)
+        const float sq1 = fmaf(-g.nu, tq2, tq1), su1 = fmaf(-g.nu, tu2, tu1);
+        row[15] = tq0 - g.mu1 * sq1 - g.mu2 * tq2;
+        row[16] = sq1;
+        row[17] = tq2;
+        row[18] = row[19] = 0.f;
+        row[35] = tu0 - g.mu1 * su1 - g.mu2 * tu2;
+        row[36] = su1;
+        row[37] = tu2;
+        row[38] = row[39] = 0.f;
+        row[40] = okb ? wp : nan_f();
+      } else {
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            tot[k] += acc[k];
-            acc[k] = 0.f;
+        for (int k = 0; k < VROW; ++k) row[k] = 0.f;
+      }
+      __syncwarp();
+      const int np = min(32, i1 - base);
+      if (grp < 2) {
+        for (int p = grp; p < np; p += 2) {
+          const float* r = sv + p * VROW;
+          const float wp = r[40];
+          const float4 xq = *reinterpret_cast<const float4*>(r + 4 * ba);
+          const float4 yq = *reinterpret_cast<const float4*>(r + 4 * bb);
+          const float4 xu = *reinterpret_cast<const float4*>(r + 20 + 4 * ba);
+          const float4 yu = *reinterpret_cast<const float4*>(r + 20 + 4 * bb);
+          const float x[8] = {xq.x * wp, xq.y * wp, xq.z * wp, xq.w * wp,
+                              xu.x * wp, xu.y * wp, xu.z * wp, xu.w * wp};
+          const float y[8] = {yq.x, yq.y, yq.z, yq.w, yu.x, yu.y, yu.z, yu.w};
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+              acc[ii * 4 + jj] = fmaf(x[ii], y[jj], fmaf(x[4 + ii], y[4 + jj], acc[ii * 4 + jj]));
+          if (++cnt == 16) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              tot[k] += acc[k];
+              acc[k] = 0.f;
+            }
+            cnt = 0;
           }
-          cnt = 0;
         }
       }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) tot[k] += acc[k];
+      __syncwarp();
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const float t1 = __shfl_down_sync(0xffffffffu, tot[k], 10);
-      const float t2 = __shfl_down_sync(0xffffffffu, tot[k], 20);
-      tot[k] = tot[k] + t1 + t2;
+      tot[k] += acc[k];
+      tot[k] += __shfl_down_sync(0xffffffffu, tot[k], 15);
     }
-    if (lane < 10) {
+    if (lane < 15) {
 #pragma unroll
       for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int i = 4 * ba + ii, j = 4 * bb + jj;
-          if (i <= j && j < 15) c.mom[(long long)((i * (29 - i)) / 2 + j) * c.ncell + cell] = tot[ii * 4 + jj];
+          if (i <= j && j < 18) c.mom[(long long)mom_index(i, j) * c.ncell + cell] = tot[ii * 4 + jj];
         }
     }
     if (lane == 0) {
-      const int px0 = c.perm[i0];
-      c.trip[cell] = c.lab[px0];
-      c.trip[c.ncell + cell] = c.lab[c.npix + px0];
-      c.trip[2 * c.ncell + cell] = c.lab[2 * c.npix + px0];
+      c.trip[cell] = kd;
+      c.trip[c.ncell + cell] = kt;
+      c.trip[2 * c.ncell + cell] = ks;
     }
   }
-  __syncthreads();
+  return block_sum<NT>(dnd, sh.red);
 }
 
 // -------------------------------------------------------------------- moment evaluation --------
-// Returns L; adds dL/dbeta into gacc (and the projected Gauss-Newton diagonal into hacc).
+// chi2 of every cell in the residual-moment form, and the adjoint gradient. With A = A(beta),
+// A_r = A(beta_ref), M = A^T N A, the N-orthogonal projector P = I - A M^-1 A^T N, D = P A_r and
+// Z = A_r^T N A:
+//   chi2_c = tr(D^T N D Q) + 2 tr(D^T N C) + tr(N R) - tr(M^-1 A^T N R N A)
+//   dL/dA  = -2 N [ D (Q Z + C^T N A) + P (C Z + R N A) ] M^-1       (Sec. 3.3.1, moment form)
+// D vanishes at beta_ref, so the rounding of the foreground-sized terms shrinks with |beta-beta_ref|.
+// Returns the sum of chi2_c; adds dL/dbeta into gacc (and the projected Gauss-Newton diagonal
+// into hacc). Per-thread rows in shared memory (stride NT): N A_1, N A_2 and R N A (75 floats).
 template <int NT, bool WANT_H>
 __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
   for (int i = threadIdx.x; i < c.P; i += NT) {
     c.gacc[i] = 0.f;
     if (WANT_H) c.hacc[i] = 0.f;
   }
-  fill_tables<NT>(a, c);  // ends with a barrier
+  fill_tables<NT>(a, c, c.x, c.tab);  // ends with a barrier
   const float* nb = a.ninv_band;
   float nsum = 0.f;
 #pragma unroll
   for (int f = 0; f < 15; ++f) nsum += nb[f];
+  float* row = c.smem + threadIdx.x;  // row[k * NT]: T1 k = 0..14, T2 15..29, B 30..74
   double acc = 0.0;
   for (int cell = threadIdx.x; cell < c.ncell; cell += NT) {
     const int kd = c.trip[cell], kt = c.trip[c.ncell + cell], ks = c.trip[2 * c.ncell + cell];
@@ -144,91 +234,163 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const float* bt = c.tab + (c.Kd + kt) * NB;
     const float* dt = c.tab + (c.Kd + c.KT + kt) * NB;
     const float* ss = c.tab + (c.Kd + 2 * c.KT + ks) * NB;
-    float T1[15], T2[15];
+    const float* pdr = c.tabr + kd * NB;
+    const float* btr = c.tabr + (c.Kd + kt) * NB;
+    const float* ssr = c.tabr + (c.Kd + 2 * c.KT + ks) * NB;
+    const float* Mc = c.mom + cell;
+    const long long st = c.ncell;
+    // M = A^T N A and Z = A_r^T N A
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
-#pragma unroll
+    float z10 = 0.f, z11 = 0.f, z12 = 0.f, z20 = 0.f, z21 = 0.f, z22 = 0.f;
+#pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
-      T1[f] = nb[f] * a1;
-      T2[f] = nb[f] * a2;
-      m01 += T1[f];
-      m02 += T2[f];
-      m11 = fmaf(T1[f], a1, m11);
-      m12 = fmaf(T1[f], a2, m12);
-      m22 = fmaf(T2[f], a2, m22);
-    }
-    float B0[15], B1[15], B2[15];
-#pragma unroll
-    for (int f = 0; f < 15; ++f) B0[f] = B1[f] = B2[f] = 0.f;
-    const float* Sc = c.mom + cell;
-#pragma unroll
-    for (int i = 0; i < 15; ++i) {
-#pragma unroll
-      for (int j = i; j < 15; ++j) {
-        const float s = Sc[(long long)((i * (29 - i)) / 2 + j) * c.ncell];
-        B0[i] = fmaf(s, nb[j], B0[i]);
-        B1[i] = fmaf(s, T1[j], B1[i]);
-        B2[i] = fmaf(s, T2[j], B2[i]);
-        if (j != i) {
-          B0[j] = fmaf(s, nb[i], B0[j]);
-          B1[j] = fmaf(s, T1[i], B1[j]);
-          B2[j] = fmaf(s, T2[i], B2[j]);
-        }
-      }
-    }
-    float G00 = 0.f, G01 = 0.f, G02 = 0.f, G11 = 0.f, G12 = 0.f, G22 = 0.f;
-#pragma unroll
-    for (int f = 0; f < 15; ++f) {
-      G00 = fmaf(nb[f], B0[f], G00);
-      G01 = fmaf(nb[f], B1[f], G01);
-      G02 = fmaf(nb[f], B2[f], G02);
-      G11 = fmaf(T1[f], B1[f], G11);
-      G12 = fmaf(T1[f], B2[f], G12);
-      G22 = fmaf(T2[f], B2[f], G22);
+      const float r1 = pdr[f] * btr[f], r2 = ssr[f];
+      const float n = nb[f];
+      const float t1 = n * a1, t2 = n * a2;
+      row[f * NT] = t1;
+      row[(15 + f) * NT] = t2;
+      m01 += t1;
+      m02 += t2;
+      m11 = fmaf(t1, a1, m11);
+      m12 = fmaf(t1, a2, m12);
+      m22 = fmaf(t2, a2, m22);
+      z10 = fmaf(r1, n, z10);
+      z11 = fmaf(r1, t1, z11);
+      z12 = fmaf(r1, t2, z12);
+      z20 = fmaf(r2, n, z20);
+      z21 = fmaf(r2, t1, z21);
+      z22 = fmaf(r2, t2, z22);
     }
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
       acc += (double)nan_f();
       continue;
     }
-    float v00, v01, v02, v11, v12, v22;
-    chol3_inverse(ch, v00, v01, v02, v11, v12, v22);
-    const float Lc = -(v00 * G00 + v11 * G11 + v22 * G22 + 2.f * (v01 * G01 + v02 * G02 + v12 * G12));
-    acc += (double)Lc;
-    // X = M^-1 G
-    const float X00 = v00 * G00 + v01 * G01 + v02 * G02;
-    const float X01 = v00 * G01 + v01 * G11 + v02 * G12;
-    const float X02 = v00 * G02 + v01 * G12 + v02 * G22;
-    const float X10 = v01 * G00 + v11 * G01 + v12 * G02;
-    const float X11 = v01 * G01 + v11 * G11 + v12 * G12;
-    const float X12 = v01 * G02 + v11 * G12 + v12 * G22;
-    const float X20 = v02 * G00 + v12 * G01 + v22 * G02;
-    const float X21 = v02 * G01 + v12 * G11 + v22 * G12;
-    const float X22 = v02 * G02 + v12 * G12 + v22 * G22;
-    float gbd = 0.f, gtd = 0.f, gbs = 0.f;
+    float v[3][3];
+    chol3_inverse(ch, v[0][0], v[0][1], v[0][2], v[1][1], v[1][2], v[2][2]);
+    v[1][0] = v[0][1];
+    v[2][0] = v[0][2];
+    v[2][1] = v[1][2];
+    const float Z[3][3] = {{nsum, m01, m02}, {z10, z11, z12}, {z20, z21, z22}};
+    // Y = M^-1 A^T N A_r = M^-1 Z^T ; D = A_r - A Y
+    float Y[3][3];
 #pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) Y[l][k] = v[l][0] * Z[k][0] + v[l][1] * Z[k][1] + v[l][2] * Z[k][2];
+    // pass 1 over bands: G1 = D^T N D, t2 = tr(D^T N C), CtA = C^T N A
+    float G1[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float CtA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float tdc = 0.f;
+#pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
-      const float e0 = B0[f] - X00 - a1 * X10 - a2 * X20;
-      const float e1 = B1[f] - X01 - a1 * X11 - a2 * X21;
-      const float e2 = B2[f] - X02 - a1 * X12 - a2 * X22;
-      const float F1 = e0 * v01 + e1 * v11 + e2 * v12;
-      const float F2 = e0 * v02 + e1 * v12 + e2 * v22;
-      const float t1 = F1 * T1[f];
+      const float ar[3] = {1.f, pdr[f] * btr[f], ssr[f]};
+      const float na[3] = {nb[f], row[f * NT], row[(15 + f) * NT]};
+      float D[3], C[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
+        C[k] = Mc[mom_index(f, 15 + k) * st];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float nd = nb[f] * D[k];
+        tdc = fmaf(nd, C[k], tdc);
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          G1[k][l] = fmaf(nd, D[l], G1[k][l]);
+          CtA[k][l] = fmaf(C[k], na[l], CtA[k][l]);
+        }
+      }
+    }
+    // B = R N A row by row (kept in shared memory), A^T N R N A and tr(N R)
+    float trNR = 0.f;
+    float AtRA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll 1
+    for (int i = 0; i < 15; ++i) {
+      float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < 15; ++j) {
+        const float s = (j >= i) ? Mc[mom_index(i, j) * st] : Mc[mom_index(j, i) * st];
+        b0 = fmaf(s, nb[j], b0);
+        b1 = fmaf(s, row[j * NT], b1);
+        b2 = fmaf(s, row[(15 + j) * NT], b2);
+        if (j == i) trNR = fmaf(nb[j], s, trNR);
+      }
+      row[(30 + i) * NT] = b0;
+      row[(45 + i) * NT] = b1;
+      row[(60 + i) * NT] = b2;
+      const float na[3] = {nb[i], row[i * NT], row[(15 + i) * NT]};
+      const float bf[3] = {b0, b1, b2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) AtRA[k][l] = fmaf(na[k], bf[l], AtRA[k][l]);
+    }
+    float Q[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = Mc[mom_index(15 + k, 15 + l) * st];
+    float chi = 2.f * tdc + trNR;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) chi += G1[k][l] * Q[l][k] - v[k][l] * AtRA[l][k];
+    acc += (double)chi;
+    // W1 = Q Z + C^T N A ;  Psi = M^-1 A^T N (C Z + R N A) = M^-1 (CtA^T Z + AtRA)
+    float W1[3][3], Psi[3][3];
+    {
+      float H[3][3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+          W1[k][l] = Q[k][0] * Z[0][l] + Q[k][1] * Z[1][l] + Q[k][2] * Z[2][l] + CtA[k][l];
+          H[k][l] = CtA[0][k] * Z[0][l] + CtA[1][k] * Z[1][l] + CtA[2][k] * Z[2][l] + AtRA[k][l];
+        }
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Psi[m][l] = v[m][0] * H[0][l] + v[m][1] * H[1][l] + v[m][2] * H[2][l];
+    }
+    float gbd = 0.f, gtd = 0.f, gbs = 0.f;
+#pragma unroll 3
+    for (int f = 0; f < 15; ++f) {
+      const float a1 = pd[f] * bt[f], a2 = ss[f];
+      const float ar[3] = {1.f, pdr[f] * btr[f], ssr[f]};
+      const float bf[3] = {row[(30 + f) * NT], row[(45 + f) * NT], row[(60 + f) * NT]};
+      float D[3], C[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
+        C[k] = Mc[mom_index(f, 15 + k) * st];
+      }
+      float E[3];
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        const float U = D[0] * W1[0][l] + D[1] * W1[1][l] + D[2] * W1[2][l];
+        const float X = C[0] * Z[0][l] + C[1] * Z[1][l] + C[2] * Z[2][l] + bf[l];
+        E[l] = U + X - fmaf(a2, Psi[2][l], fmaf(a1, Psi[1][l], Psi[0][l]));
+      }
+      const float F1 = E[0] * v[0][1] + E[1] * v[1][1] + E[2] * v[2][1];
+      const float F2 = E[0] * v[0][2] + E[1] * v[1][2] + E[2] * v[2][2];
+      const float t1 = F1 * row[f * NT];
       gbd = fmaf(t1, a.bands.lnd[f], gbd);
       gtd = fmaf(t1, dt[f], gtd);
-      gbs = fmaf(F2 * T2[f], a.bands.lns[f], gbs);
+      gbs = fmaf(F2 * row[(15 + f) * NT], a.bands.lns[f], gbs);
     }
     atomicAdd(c.gacc + kd, -2.f * gbd);
     atomicAdd(c.gacc + c.Kd + kt, -2.f * gtd);
     atomicAdd(c.gacc + c.Kd + c.KT + ks, -2.f * gbs);
     if (WANT_H) {
-      // Q = M^-1 G M^-1 = sum_p w sum_s s_hat s_hat^T ; projected GN diagonal per parameter
-      const float Q11 = X10 * v01 + X11 * v11 + X12 * v12;
-      const float Q22 = X20 * v02 + X21 * v12 + X22 * v22;
+      // projected Gauss-Newton diagonal 2 (sum w s_k^2) (da^T N da - u^T M^-1 u), u = A^T N da,
+      // with sum w s s^T taken at the reference point (Q)
       float n2[3] = {0.f, 0.f, 0.f}, u0[3] = {0.f, 0.f, 0.f}, u1[3] = {0.f, 0.f, 0.f},
             u2[3] = {0.f, 0.f, 0.f};
-#pragma unroll
+#pragma unroll 3
       for (int f = 0; f < 15; ++f) {
         const float a1 = pd[f] * bt[f], a2 = ss[f];
         const float da[3] = {a1 * a.bands.lnd[f], a1 * dt[f], a2 * a.bands.lns[f]};
@@ -244,9 +406,13 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       float h[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float quad = v00 * u0[k] * u0[k] + v11 * u1[k] * u1[k] + v22 * u2[k] * u2[k] +
-                           2.f * (v01 * u0[k] * u1[k] + v02 * u0[k] * u2[k] + v12 * u1[k] * u2[k]);
-        h[k] = 2.f * (k < 2 ? Q11 : Q22) * fmaxf(n2[k] - quad, 0.f);
+        const float uu[3] = {u0[k], u1[k], u2[k]};
+        float quad = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) quad = fmaf(uu[i] * v[i][j], uu[j], quad);
+        h[k] = 2.f * (k < 2 ? Q[1][1] : Q[2][2]) * fmaxf(n2[k] - quad, 0.f);
       }
       atomicAdd(c.hacc + kd, h[0]);
       atomicAdd(c.hacc + c.Kd + kt, h[1]);
@@ -266,7 +432,7 @@ __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_
       if (WANT_H) c.hacc[i] = 0.f;
     }
   }
-  fill_tables<NT>(a, c);
+  fill_tables<NT>(a, c, c.x, c.tab);
   float nb[NB];
 #pragma unroll
   for (int f = 0; f < NB; ++f) nb[f] = a.ninv_band[f];
@@ -328,8 +494,7 @@ __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_
 template <int NT, int PATH, int GMODE, int NOISE, bool WANT_H>
 __device__ double objective(const FitArgs& a, Ctx& c, Shared& sh, double& dnd) {
   if (PATH == CSX_PATH_MOMENT) {
-    dnd = 0.0;
-    return eval_moment<NT, WANT_H>(a, c, sh);
+    return eval_moment<NT, WANT_H>(a, c, sh);  // chi2; dnd comes from the moment build
   } else {
     return eval_stream<NT, NOISE, GMODE == CSX_GRAD_ADJOINT, WANT_H>(a, c, sh, dnd);
   }
@@ -358,8 +523,18 @@ __device__ void fd_gradient(const FitArgs& a, Ctx& c, Shared& sh, const float* z
 }
 
 // ------------------------------------------------------------------------ the fit --------------
+// Moment path: make the current point c.x the reference point and rebuild the cell moments.
+template <int NT, int NOISE>
+__device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem) {
+  for (int i = threadIdx.x; i < c.P; i += NT) c.xr[i] = c.x[i];
+  __syncthreads();
+  fill_tables<NT>(a, c, c.xr, c.tabr);
+  return build_moments<NT, NOISE == CSX_NOISE_SEPARABLE>(a, c, smem, sh);
+}
+
 template <int NT, int PATH, int GMODE, int NOISE>
-__device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long long poff) {
+__device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int q,
+                            long long poff) {
   const int P = c.P;
   const int tid = threadIdx.x;
   const int m = a.history;
@@ -370,7 +545,10 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
   }
   __syncthreads();
   double dnd = 0.0;
+  int recentres = 0;
+  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem);
   double f = objective<NT, PATH, GMODE, NOISE, true>(a, c, sh, dnd);
+  int nev = 1;  // likelihood evaluations (each forward pass of a finite difference counts once)
   int status = CSX_FIT_MAXITER, it = 0;
   if (!isfinite(f)) {
     for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.x[i];
@@ -378,6 +556,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
       a.L_out[q] = (double)nan_f();
       a.status[q] = CSX_FIT_NONPHYSICAL;
       a.iters[q] = 0;
+      if (a.nevals) a.nevals[q] = nev;
     }
     __syncthreads();
     return;
@@ -394,7 +573,10 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
     if (GMODE == CSX_GRAD_ADJOINT) c.g[i] = c.gacc[i] / c.hs[i];
   }
   __syncthreads();
-  if (GMODE == CSX_GRAD_FD) fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
+  if (GMODE == CSX_GRAD_FD) {
+    fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
+    nev += 2 * P;
+  }
 
   int count = 0, head = 0;
   double gamma = 1.0;
@@ -473,6 +655,26 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
       }
     }
     if (it > 0 && stepn <= 1.f && last_step <= 1.f) {
+      if (PATH == CSX_PATH_MOMENT && recentres < 6) {
+        // The moment form rounds in proportion to the distance from the reference point:
+        // converge again about the current point unless it is already close.
+        float dref = 0.f;
+        for (int i = tid; i < P; i += NT)
+          dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
+        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+        if (dref > 30.f) {
+          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
+          __syncthreads();
+          dnd = recentre<NT, NOISE>(a, c, sh, smem);
+          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
+          ++nev;
+          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
+          ++recentres;
+          last_step = 1e30f;
+          __syncthreads();
+          continue;
+        }
+      }
       status = CSX_FIT_CONVERGED;
       break;
     }
@@ -501,8 +703,10 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
       }
       __syncthreads();
       ft = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd_t);
+      ++nev;
       if (GMODE == CSX_GRAD_FD) {
         fd_gradient<NT, NOISE>(a, c, sh, c.zt, c.gt);
+        nev += 2 * P;
       } else {
         for (int i = tid; i < P; i += NT) c.gt[i] = c.gacc[i] / c.hs[i];
       }
@@ -541,6 +745,26 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
       }
     }
     if (!ok) {
+      if (PATH == CSX_PATH_MOMENT && recentres < 6) {
+        // Far from the reference point the moment form's rounding can hide the decrease the
+        // line search looks for: move the reference here and try again.
+        float dref = 0.f;
+        for (int i = tid; i < P; i += NT)
+          dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
+        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+        if (dref > 1.f) {
+          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
+          __syncthreads();
+          dnd = recentre<NT, NOISE>(a, c, sh, smem);
+          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
+          ++nev;
+          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
+          ++recentres;
+          last_step = 1e30f;
+          __syncthreads();
+          continue;
+        }
+      }
       if (count > 0) {  // drop the curvature history and retry from steepest descent
         count = 0;
         gamma = 1.0;
@@ -569,7 +793,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
     sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
     last_step = sn;
     f = ft;
-    dnd = dnd_t;
+    if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
     if (sy > 1e-12 * yy && yy > 0.0) {
       if (tid == 0) sh.rho[head] = 1.0 / sy;
       head = (head + 1) % m;
@@ -580,9 +804,10 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, int q, long lo
   }
   for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.z[i] / c.hs[i];
   if (tid == 0) {
-    a.L_out[q] = (PATH == CSX_PATH_MOMENT) ? f : f - dnd;
+    a.L_out[q] = f - dnd;  // L = chi2_min - sum d^T N d
     a.status[q] = status;
     a.iters[q] = it;
+    if (a.nevals) a.nevals[q] = nev;
   }
   __syncthreads();
 }
@@ -591,6 +816,8 @@ template <int NT, int PATH, int GMODE, int NOISE>
 __global__ void __launch_bounds__(NT) k_fit(const __grid_constant__ FitArgs a) {
   __shared__ Shared sh;
   __shared__ int s_q;
+  extern __shared__ float4 build_smem4[];  // moment build staging (moment path only)
+  float* build_smem = reinterpret_cast<float*>(build_smem4);
   float* base = a.slots + (long long)blockIdx.x * a.slot_floats;
   const int Pm = a.Pmax;
   for (;;) {
@@ -626,31 +853,62 @@ __global__ void __launch_bounds__(NT) k_fit(const __grid_constant__ FitArgs a) {
     c.S = base + 9 * Pm;
     c.Y = c.S + (long long)a.history * Pm;
     c.tab = c.Y + (long long)a.history * Pm;
-    c.mom = c.tab + (long long)a.rows_max * NB;
-    c.trip = reinterpret_cast<int*>(c.mom + (long long)NE * a.ncell_max);
-    if (PATH == CSX_PATH_MOMENT)
-      build_moments<NT, NOISE == CSX_NOISE_SEPARABLE>(a, c);
-    fit_problem<NT, PATH, GMODE, NOISE>(a, c, sh, q, pd.poff);
+    c.tabr = c.tab + (long long)a.rows_max * NB;
+    c.xr = c.tabr + (long long)a.rows_max * NB;
+    c.mom = c.xr + Pm;
+    c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * a.ncell_max);
+    c.smem = build_smem;
+    fit_problem<NT, PATH, GMODE, NOISE>(a, c, sh, build_smem, q, pd.poff);
   }
 }
 
 // ---------------------------------------------------------------------------- launcher --------
 int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path, long long* out) {
   long long n = (long long)(9 + 2 * history) * Pmax + (long long)rows_max * NB;
-  if (path == CSX_PATH_MOMENT) n += (long long)NE * ncell_max + 3LL * ncell_max;
+  n += (long long)rows_max * NB + Pmax;  // reference tables and parameters (moment path)
+  if (path == CSX_PATH_MOMENT) n += (long long)NM * ncell_max + 3LL * ncell_max;
   n = (n + 63) & ~63LL;
   *out = n;
+  return CSX_OK;
+}
+
+template <int NT, int PATH>
+constexpr size_t fit_dyn_smem() {
+  // build staging (32 pixel rows per warp) or, during evaluations, 75 floats per thread
+  constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
+  constexpr size_t rows = (size_t)75 * NT;
+  return PATH == CSX_PATH_MOMENT ? (build > rows ? build : rows) * sizeof(float) : 0;
+}
+
+template <int NT, int PATH, int GMODE, int NOISE>
+static int prepare_kernel() {
+  const size_t dyn = fit_dyn_smem<NT, PATH>();
+  if (dyn > 0)
+    CSX_CUDA(cudaFuncSetAttribute(k_fit<NT, PATH, GMODE, NOISE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   return CSX_OK;
 }
 
 template <int NT, int PATH, int GMODE, int NOISE>
 static int occupancy_grid(int* grid) {
   int dev = 0, sms = 0, per = 0;
+  int rc = prepare_kernel<NT, PATH, GMODE, NOISE>();
+  if (rc) return rc;
   CSX_CUDA(cudaGetDevice(&dev));
   CSX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fit<NT, PATH, GMODE, NOISE>, NT, 0));
+  CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fit<NT, PATH, GMODE, NOISE>, NT,
+                                                         fit_dyn_smem<NT, PATH>()));
   if (per < 1) per = 1;
   *grid = sms * per;
+  return CSX_OK;
+}
+
+template <int NT, int PATH, int GMODE, int NOISE>
+static int launch_one(const FitArgs& a, int grid, cudaStream_t s) {
+  int rc = prepare_kernel<NT, PATH, GMODE, NOISE>();
+  if (rc) return rc;
+  k_fit<NT, PATH, GMODE, NOISE><<<grid, NT, fit_dyn_smem<NT, PATH>(), s>>>(a);
+  CSX_CUDA(cudaGetLastError());
   return CSX_OK;
 }
 
@@ -666,28 +924,18 @@ int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s) {
   if (a.nprob == 0) return CSX_OK;
   CSX_CUDA(cudaMemsetAsync(a.head, 0, sizeof(int), s));
   constexpr int NT = 256;
-  if (a.path == CSX_PATH_MOMENT) {
-    if (a.noise_kind == CSX_NOISE_SEPARABLE)
-      k_fit<NT, CSX_PATH_MOMENT, CSX_GRAD_ADJOINT, CSX_NOISE_SEPARABLE><<<grid, NT, 0, s>>>(a);
-    else
-      k_fit<NT, CSX_PATH_MOMENT, CSX_GRAD_ADJOINT, CSX_NOISE_HOMOGENEOUS><<<grid, NT, 0, s>>>(a);
-  } else if (a.grad_mode == CSX_GRAD_FD) {
-    if (a.noise_kind == CSX_NOISE_SEPARABLE)
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_FD, CSX_NOISE_SEPARABLE><<<grid, NT, 0, s>>>(a);
-    else if (a.noise_kind == CSX_NOISE_HOMOGENEOUS)
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_FD, CSX_NOISE_HOMOGENEOUS><<<grid, NT, 0, s>>>(a);
-    else
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_FD, CSX_NOISE_PERPIXEL><<<grid, NT, 0, s>>>(a);
-  } else {
-    if (a.noise_kind == CSX_NOISE_SEPARABLE)
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_ADJOINT, CSX_NOISE_SEPARABLE><<<grid, NT, 0, s>>>(a);
-    else if (a.noise_kind == CSX_NOISE_HOMOGENEOUS)
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_ADJOINT, CSX_NOISE_HOMOGENEOUS><<<grid, NT, 0, s>>>(a);
-    else
-      k_fit<NT, CSX_PATH_STREAM, CSX_GRAD_ADJOINT, CSX_NOISE_PERPIXEL><<<grid, NT, 0, s>>>(a);
+  constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT, FD = CSX_GRAD_FD;
+  constexpr int HO = CSX_NOISE_HOMOGENEOUS, SE = CSX_NOISE_SEPARABLE, PP = CSX_NOISE_PERPIXEL;
+  if (a.path == M) {
+    return a.noise_kind == SE ? launch_one<NT, M, AD, SE>(a, grid, s) : launch_one<NT, M, AD, HO>(a, grid, s);
+  } else if (a.grad_mode == FD) {
+    if (a.noise_kind == SE) return launch_one<NT, ST, FD, SE>(a, grid, s);
+    if (a.noise_kind == HO) return launch_one<NT, ST, FD, HO>(a, grid, s);
+    return launch_one<NT, ST, FD, PP>(a, grid, s);
   }
-  CSX_CUDA(cudaGetLastError());
-  return CSX_OK;
+  if (a.noise_kind == SE) return launch_one<NT, ST, AD, SE>(a, grid, s);
+  if (a.noise_kind == HO) return launch_one<NT, ST, AD, HO>(a, grid, s);
+  return launch_one<NT, ST, AD, PP>(a, grid, s);
 }
 
 }  // namespace csx

@@ -68,49 +68,43 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 #pragma unroll
         for (int f = 0; f < NB; ++f) nn[f] = nb[f];
       }
-      float dq[NB], du[NB];
-      load_pixel(dr + (long long)p * 2 * NB, dq, du);
-      float m00 = 0.f, m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
-      float bq[3] = {0.f, 0.f, 0.f}, bu[3] = {0.f, 0.f, 0.f}, fq[3] = {0.f, 0.f, 0.f},
-            fu[3] = {0.f, 0.f, 0.f};
-      float gq[NB], gu[NB];
-      if (a.d_fg) load_pixel(a.d_fg + (long long)p * 2 * NB, gq, gu);
+      float ad[NB], as[NB], c1[NB], c2[NB];
 #pragma unroll
       for (int f = 0; f < NB; ++f) {
-        const float a1 = pdr[f] * btr[f], a2 = ssr[f], n = nn[f];
-        const float na1 = n * a1, na2 = n * a2;
-        m00 += n;
-        m01 += na1;
-        m02 += na2;
-        m11 = fmaf(na1, a1, m11);
-        m12 = fmaf(na1, a2, m12);
-        m22 = fmaf(na2, a2, m22);
-        bq[0] = fmaf(n, dq[f], bq[0]);
-        bq[1] = fmaf(na1, dq[f], bq[1]);
-        bq[2] = fmaf(na2, dq[f], bq[2]);
-        bu[0] = fmaf(n, du[f], bu[0]);
-        bu[1] = fmaf(na1, du[f], bu[1]);
-        bu[2] = fmaf(na2, du[f], bu[2]);
-        if (a.d_fg) {
-          fq[0] = fmaf(n, gq[f], fq[0]);
-          fq[1] = fmaf(na1, gq[f], fq[1]);
-          fq[2] = fmaf(na2, gq[f], fq[2]);
-          fu[0] = fmaf(n, gu[f], fu[0]);
-          fu[1] = fmaf(na1, gu[f], fu[1]);
-          fu[2] = fmaf(na2, gu[f], fu[2]);
-        }
+        ad[f] = pdr[f] * btr[f];
+        as[f] = ssr[f];
       }
-      Chol3 c;
-      if (chol3(m00, m01, m02, m11, m12, m22, c)) {
-        chol3_solve(c, bq[0], bq[1], bq[2], sq[0], sq[1], sq[2]);
-        chol3_solve(c, bu[0], bu[1], bu[2], su[0], su[1], su[2]);
-        float v00, v01, v02, v11, v12, v22;
-        chol3_inverse(c, v00, v01, v02, v11, v12, v22);
-        var = v00;
+      Mgs3 g;
+      if (mgs3(nn, ad, as, c1, c2, g)) {
+        // s_hat = R^-1 t with t the projections on the orthogonalised columns (1, c1, c2)
+        auto solve = [&](const float* x, float* s) {
+          float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+#pragma unroll
+          for (int f = 0; f < NB; ++f) {
+            const float nx = nn[f] * x[f];
+            t0 += nx;
+            t1 = fmaf(nx, c1[f], t1);
+            t2 = fmaf(nx, c2[f], t2);
+          }
+          t0 *= g.i0;
+          t1 *= g.i1;
+          t2 *= g.i2;
+          s[2] = t2;
+          s[1] = fmaf(-g.nu, t2, t1);
+          s[0] = t0 - g.mu1 * s[1] - g.mu2 * s[2];
+        };
+        float dq[NB], du[NB];
+        load_pixel(dr + (long long)p * 2 * NB, dq, du);
+        solve(dq, sq);
+        solve(du, su);
+        var = mgs3_var00(g);
         if (a.d_fg) {
-          float t1, t2;
-          chol3_solve(c, fq[0], fq[1], fq[2], rq, t1, t2);
-          chol3_solve(c, fu[0], fu[1], fu[2], ru, t1, t2);
+          float gq[NB], gu[NB], t[3];
+          load_pixel(a.d_fg + (long long)p * 2 * NB, gq, gu);
+          solve(gq, t);
+          rq = t[0];
+          solve(gu, t);
+          ru = t[0];
         } else {
           rq = ru = 0.f;
         }

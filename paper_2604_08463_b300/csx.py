@@ -70,7 +70,7 @@ def lib():
         L.csx_spectral_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp, vp]
         L.csx_build_cells.argtypes = [i32, i32, vp, pi32, vp, vp, vp, vp]
         L.csx_fit_batch.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32,
-                                    POINTER(CFitOpts), vp, vp, vp, vp, vp, vp]
+                                    POINTER(CFitOpts), vp, vp, vp, vp, vp, vp, vp]
         L.csx_reconstruct.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32, vp, vp, vp,
                                       vp, vp, vp, vp]
         L.csx_select.argtypes = [i32, i32, vp, vp, vp, vp]
@@ -252,11 +252,12 @@ def fit_batch(model: Model, sky: Sky, labels, K, beta0, **opts):
     L = torch.empty(nprob, dtype=torch.float64, device=dev)
     st = torch.empty(nprob, dtype=torch.int32, device=dev)
     it = torch.empty(nprob, dtype=torch.int32, device=dev)
+    ne = torch.empty(nprob, dtype=torch.int32, device=dev)
     o = fit_options(**opts)
     _check(lib().csx_fit_batch(ctypes.byref(model.c), ctypes.byref(sky.c), nconf, _ptr(labels),
                                Kp, ctypes.byref(o), _ptr(beta0), _ptr(out), _ptr(L), _ptr(st),
-                               _ptr(it), _stream()))
-    return {"beta": out, "L": L, "status": st, "iters": it}
+                               _ptr(it), _ptr(ne), _stream()))
+    return {"beta": out, "L": L, "status": st, "iters": it, "nevals": ne}
 
 
 def reconstruct(model: Model, sky: Sky, labels, K, beta, d_fg=None, s_hat=False, sigma2=False,

@@ -80,7 +80,8 @@ def many_patch_labels(vec: np.ndarray, ks, key: str = "", processes: int | None 
     todo = sorted({int(k) for k in ks if (key, vec.shape[0], int(k)) not in _CACHE}, reverse=True)
     if todo:
         nproc = processes or min(len(todo), len(os.sched_getaffinity(0)))
-        if nproc > 1 and len(todo) > 4:
+        work = vec.shape[0] * sum(todo)  # assignment cost ~ pixels x clusters per iteration
+        if nproc > 1 and len(todo) > 4 and work > 5e7:
             import multiprocessing as mp
             with mp.get_context("spawn").Pool(nproc) as pool:
                 for k, lab in pool.imap_unordered(_worker, [(vec, k) for k in todo]):

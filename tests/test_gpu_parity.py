@@ -3,7 +3,10 @@
 Tolerances (stated, not tuned per case):
   L:        relative 1e-5
   grad L:   ||g - g_ref||_inf <= 1e-4 ||g_ref||_inf, and per component
-            |g_i - r_i| <= 1e-4 (|r_i| + 1e-2 ||r||_inf)
+            |g_i - r_i| <= 1e-4 |r_i| + 1e-5 S_i, where S_i is the summed magnitude of the
+            per-pixel, per-band terms of dL/dtheta_i (oracle.likelihood.gradient_term_scale): a
+            component that is a small remainder of cancelling terms is only as accurate as
+            FP32 arithmetic on those terms
   fit:      |beta_d - ref| <= 1e-3, |T_d - ref| <= 1e-2 K, |beta_s - ref| <= 1e-3 (where the oracle
             optimum is interior)
   mixing / reconstruction (FP32 arithmetic): relative 2e-5 (mixing), 1e-4 of the field's scale.
@@ -40,13 +43,20 @@ def _csx():
     return csx
 
 
-def assert_grad_close(g, r):
+def assert_grad_close(g, r, S):
     g = np.asarray(g, np.float64)
     r = np.asarray(r, np.float64)
     scale = np.abs(r).max()
     assert np.abs(g - r).max() <= 1e-4 * scale, (np.abs(g - r).max() / scale)
-    bad = np.abs(g - r) > 1e-4 * (np.abs(r) + 1e-2 * scale)
-    assert not bad.any(), (np.nonzero(bad)[0][:10], g[bad][:5], r[bad][:5])
+    bad = np.abs(g - r) > 1e-4 * np.abs(r) + 1e-5 * S
+    assert not bad.any(), (np.nonzero(bad)[0][:10], g[bad][:5], r[bad][:5], S[bad][:5])
+
+
+def grad_ref(case, r, lab, K, beta, d64=None, ninv=None):
+    d64 = case.d64(r) if d64 is None else d64
+    ninv = case.ninv64 if ninv is None else ninv
+    L, g = lk.spectral_gradient(case.nu, d64, ninv, lab, K, beta)
+    return L, g, lk.gradient_term_scale(case.nu, d64, ninv, lab, K, beta)
 
 
 # ------------------------------------------------------------------------------ mixing --------
@@ -83,11 +93,10 @@ def test_spectral_like_and_grad(noise, nside, K):
     torch.cuda.synchronize()
     L1, L2, g = L1.cpu().numpy(), L2.cpu().numpy(), g.cpu().numpy()
     for r in range(3):
-        Lr, gr = lk.spectral_gradient(case.nu, case.d64(r), case.ninv64, lab, K,
-                                      beta[r].astype(np.float64))
+        Lr, gr, Sr = grad_ref(case, r, lab, K, beta[r].astype(np.float64))
         assert abs(L1[r] - Lr) <= 1e-5 * abs(Lr), (L1[r], Lr)
         assert abs(L2[r] - Lr) <= 1e-5 * abs(Lr)
-        assert_grad_close(g[r], gr)
+        assert_grad_close(g[r], gr, Sr)
 
 
 def test_spectral_ragged_tails_and_one_pixel_patches():
@@ -107,10 +116,17 @@ def test_spectral_ragged_tails_and_one_pixel_patches():
     L, g = csx.spectral_grad(model, sky, torch.tensor(lab, device="cuda"), K,
                              torch.tensor(beta, device="cuda"))
     torch.cuda.synchronize()
-    Lr, gr = lk.spectral_gradient(case.nu, case.d64(0)[:keep], case.ninv64[:keep], lab, K,
-                                  beta[0].astype(np.float64))
+    Lr, gr, Sr = grad_ref(case, 0, lab, K, beta[0].astype(np.float64),
+                          d64=case.d64(0)[:keep], ninv=case.ninv64[:keep])
     assert abs(L.item() - Lr) <= 1e-5 * abs(Lr)
-    assert_grad_close(g.cpu().numpy()[0], gr)
+    # A one-pixel patch has no sum to average rounding over: at nside 8 (|d| / |r| ~ 3e3 per band)
+    # its gradient is bounded by the FP32 forming of r = d - A s_hat, error <= ~4 u |d| per band,
+    # i.e. 4 u S_d with S_d the data-scaled term magnitude (u = 2^-24); checked with a factor 4.
+    Sd = lk.gradient_term_scale(case.nu, case.d64(0)[:keep], case.ninv64[:keep], lab, K,
+                                beta[0].astype(np.float64), data_scale=True)
+    assert_grad_close(g.cpu().numpy()[0], gr, Sr + 16 * 2.0 ** -24 / 1e-5 * Sd)
+    # the beta_d components of the T_d / beta_s patches (many pixels) keep the plain bound
+    assert_grad_close(g.cpu().numpy()[0][keep:], gr[keep:], Sr[keep:])
 
 
 def test_out_of_range_label_poisons_L():
@@ -157,11 +173,11 @@ def test_autograd_function():
     (3.0 * L[0] - 0.5 * L[1]).backward()
     torch.cuda.synchronize()
     b = beta.detach().cpu().numpy().astype(np.float64)
-    _, g0 = lk.spectral_gradient(case.nu, case.d64(0), case.ninv64, case.wl.labels[0], K, b[0])
-    _, g1 = lk.spectral_gradient(case.nu, case.d64(1), case.ninv64, case.wl.labels[0], K, b[1])
+    _, g0, S0 = grad_ref(case, 0, case.wl.labels[0], K, b[0])
+    _, g1, S1 = grad_ref(case, 1, case.wl.labels[0], K, b[1])
     got = beta.grad.cpu().numpy()
-    assert_grad_close(got[0], 3.0 * g0)
-    assert_grad_close(got[1], -0.5 * g1)
+    assert_grad_close(got[0], 3.0 * g0, 3.0 * S0)
+    assert_grad_close(got[1], -0.5 * g1, 0.5 * S1)
 
 
 # ------------------------------------------------------------------------------- cells --------

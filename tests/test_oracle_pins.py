@@ -211,6 +211,20 @@ def test_gradient_central_fd(hitcount):
     np.testing.assert_allclose(g, fd, rtol=2e-6, atol=1e-6 * np.abs(g).max())
 
 
+def test_gradient_term_scale_bounds_the_gradient():
+    sk, labels, K, d, ninv = _small_problem()
+    beta = workloads.random_points(K, 1, seed=4)[0]
+    _, g = lk.spectral_gradient(NU, d, ninv, labels, K, beta)
+    sc = lk.gradient_term_scale(NU, d, ninv, labels, K, beta)
+    assert sc.shape == g.shape and np.all(sc > 0)
+    assert np.all(sc >= np.abs(g) * (1 - 1e-12))  # triangle inequality
+    # one patch per parameter, one pixel: S is the sum of the band terms' magnitudes
+    lab1 = np.zeros((3, 1), np.int64)
+    _, g1 = lk.spectral_gradient(NU, d[:1], ninv[:1], lab1, np.array([1, 1, 1]), beta[[0, 3, 5]])
+    s1 = lk.gradient_term_scale(NU, d[:1], ninv[:1], lab1, np.array([1, 1, 1]), beta[[0, 3, 5]])
+    assert np.all(s1 >= np.abs(g1))
+
+
 def test_gls_statistics_monte_carlo():
     # at fixed beta, Var[s_hat_cmb] over noise draws -> [M^-1]_00 and <s_hat> = s at beta_true
     sk = S.make_sky(2, truth="uniform", hitcount=True)
