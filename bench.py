@@ -27,11 +27,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# seeded K-means labelings are deterministic: keep them between runs (git-ignored input cache)
+os.environ.setdefault("CSX_KMEANS_CACHE", os.path.join(ROOT, ".cache", "kmeans"))
 
 METRIC = "config fits/s & cluster-pixel L+grad L evals/s at nside64 vs plain form; % HBM peak"
 SCAN = dict(nside=64, nconf=1000, kmax=500, nreal=10, b_cut_deg=20.0)
 BYTES_PER_PIXEL_EVAL = 120 + 12 + 4   # 15 bands x Q,U float32 + 3 int32 labels + hit weight
 BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12  # residual moments (R, C, Q) + cell labels
+FLOPS_PER_CELL_EVAL = 4600   # FP32 operations of one cell's chi2 + gradient (FMA = 2)
+FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (FMA = 2)
+
+
+def fp32_peak_tflops(sm_mhz):
+    """148 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -100,10 +109,14 @@ class ClockSampler:
         if self.thread is not None:
             self.thread.join(timeout=5)
 
-    def summary(self):
+    def mark(self):
+        """Index of the next sample (to cut out the timed window)."""
+        return len(self.rows)
+
+    def summary(self, lo=0, hi=None):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in self.rows[lo:hi]:
             try:
                 sm.append(float(r[0]))
                 mx = float(r[1])
@@ -191,7 +204,10 @@ def run_csx(args):
     K = inp["K"]
     model = csx.Model(wl.sky.nu)
     sky = csx.Sky(d, noise="separable", ninv_band=inp["nb32"], w=w)
-    opts = dict(path=args.path)
+    opts = dict(path=args.path, threads=args.threads)
+    path = "stream" if args.path == "stream" else "moment"  # auto picks moment (separable noise)
+    _, _, ncell_d = csx.build_cells(labels, K)
+    ncell = ncell_d.cpu().numpy().astype(np.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -200,35 +216,55 @@ def run_csx(args):
         vt, best = csx.select(rec["metrics"], nconf, nreal)
         return res, rec, vt, best
 
+    # the clock sampler starts before the warm-up: starting nvidia-smi stalls CUDA launches briefly
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    sampler = ClockSampler(local)
-    sampler.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     fit_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
+    rec_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
     evals = []
-    e0.record(stream)
+    host_s = {"fit": 0.0, "reconstruct": 0.0, "select": 0.0}
+    mark0 = sampler.mark()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     for k in range(args.steps):
-        flush.zero_()
+        flush.zero_()  # L2 flush (outside the step for k = 0, inside the stream order otherwise)
+        if k == 0:
+            e0.record(stream)
         fit_ev[k][0].record(stream)
+        t = time.perf_counter()
         res = csx.fit_batch(model, sky, labels, K, beta0, **opts)
+        host_s["fit"] += time.perf_counter() - t
         fit_ev[k][1].record(stream)
+        rec_ev[k][0].record(stream)
+        t = time.perf_counter()
         rec = csx.reconstruct(model, sky, labels, K, res["beta"], d_fg=fg, metrics=True)
+        host_s["reconstruct"] += time.perf_counter() - t
+        t = time.perf_counter()
         vt, best = csx.select(rec["metrics"], nconf, nreal)
+        host_s["select"] += time.perf_counter() - t
+        rec_ev[k][1].record(stream)
         evals.append(res["nevals"])
     e1.record(stream)
     torch.cuda.synchronize()
+    bounds = [e0] + [a for a, _ in fit_ev[1:]] + [e1]
+    breakdown = {"fit_ms": None, "reconstruct_select_ms": statistics.mean(
+        a.elapsed_time(b) for a, b in rec_ev),
+        "host_call_ms": {k: 1e3 * v / args.steps for k, v in host_s.items()},
+        "step_ms": [bounds[i].elapsed_time(bounds[i + 1]) for i in range(args.steps)],
+        "start_to_first_fit_ms": e0.elapsed_time(fit_ev[0][0])}
+    mark1 = sampler.mark()
     if dist:
         dist.barrier()
-    sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     fit_ms = statistics.mean(a.elapsed_time(b) for a, b in fit_ev)
     ms_max = ms
@@ -240,16 +276,33 @@ def run_csx(args):
     status = res["status"].cpu().numpy()
     iters = res["iters"].cpu().numpy()
     nev = torch.stack(evals).to(torch.float64).mean(0).cpu().numpy()
-    path = "moment" if args.path == "moment" else "stream"
-    units_per_eval = npix if path == "stream" else None
+    conf_of = np.repeat(np.arange(nconf), nreal)
     if path == "stream":
         unit_evals = float(nev.sum()) * npix
         alg_bytes = unit_evals * BYTES_PER_PIXEL_EVAL
+        alg_flops = unit_evals * FLOPS_PER_PIXEL_EVAL
     else:
-        unit_evals = float(nev.sum())  # refined below by cell counts
+        unit_evals = float((nev * ncell[conf_of]).sum())
         alg_bytes = unit_evals * BYTES_PER_CELL_EVAL
+        alg_flops = unit_evals * FLOPS_PER_CELL_EVAL
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (fit_ms * 1e-3) / 1e9
+    sampler.stop()
+    clocks = sampler.summary(mark0, mark1)
+    fp32_peak = fp32_peak_tflops(clocks["sm_mhz"] or 2032.0)
+    achieved_tf = alg_flops / (fit_ms * 1e-3) / 1e12
+    # one untimed fit with the other evaluation path, for comparison
+    torch.cuda.synchronize()
+    other = "stream" if path == "moment" else "moment"
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    res_o = csx.fit_batch(model, sky, labels, K, beta0, path=other)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    other_fit = {"path": other, "fit_ms": c0.elapsed_time(c1),
+                 "converged": int((res_o["status"].cpu().numpy() == 0).sum()),
+                 "iters_mean": float(res_o["iters"].cpu().numpy().mean())}
 
     # end to end: pinned host inputs -> device, step, results -> host
     e2e = None
@@ -306,7 +359,24 @@ def run_csx(args):
             dist.destroy_process_group()
         return
     launches_per_step = 4 + (1 if path == "moment" else 0)
-    clocks = sampler.summary()
+    frac_mem, frac_alu = achieved / hbm, achieved_tf / fp32_peak
+    if frac_alu >= frac_mem:
+        roof = {"kernel": "k_fit (persistent fit)", "bound": "alu", "achieved": achieved_tf,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": frac_alu,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x median SM clock %.0f MHz"
+                               % (clocks["sm_mhz"] or 2032.0),
+                "flops_per_unit": FLOPS_PER_CELL_EVAL if path == "moment" else FLOPS_PER_PIXEL_EVAL,
+                "units": unit_evals, "traffic": None,
+                "memory_side": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": frac_mem}}
+    else:
+        roof = {"kernel": "k_fit (persistent fit)", "bound": "hbm", "achieved": achieved,
+                "peak": hbm, "unit": "GB/s", "frac": frac_mem,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_unit": BYTES_PER_CELL_EVAL if path == "moment" else BYTES_PER_PIXEL_EVAL,
+                "units": unit_evals, "traffic": None,
+                "alu_side": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
+                             "frac": frac_alu}}
+    roof["unit_kind"] = "cell evaluations" if path == "moment" else "pixel evaluations"
     line = {
         "metric": METRIC,
         "value": world * nprob / (ms_max * 1e-3),
@@ -325,18 +395,16 @@ def run_csx(args):
                    "max_P": int(wl.P.max()), "fit_path": path,
                    "l2": "256 MiB buffer written before every timed step (L2 is 126 MB)",
                    "parallelism": "weak: each rank fits its own 1000 configurations"},
-        "pixel_evals_per_s": (float(nev.sum()) * npix / (fit_ms * 1e-3)) if path == "stream" else None,
+        "cluster_pixel_evals_per_s": float(nev.sum()) * npix / (fit_ms * 1e-3),
+        "cell_evals_per_s": float((nev * ncell[conf_of]).sum()) / (fit_ms * 1e-3),
+        "mean_cells": float(ncell.mean()),
         "fit_ms": fit_ms,
+        "breakdown": dict(breakdown, fit_ms=fit_ms),
         "fit_stats": {"converged": int((status == 0).sum()), "max_iter": int((status == 1).sum()),
                       "line_search": int((status == 3).sum()), "nonphysical": int((status == 2).sum()),
                       "iters_mean": float(iters.mean()), "evals_mean": float(nev.mean())},
-        "roofline": {"kernel": "k_fit (persistent fit)", "bound": "hbm", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_unit": BYTES_PER_PIXEL_EVAL if path == "stream" else BYTES_PER_CELL_EVAL,
-                     "traffic": None,
-                     "note": "algorithmic bytes of every likelihood evaluation / fit-kernel time; the "
-                             "10 realizations' data (42 MB) stay resident in L2, so this can exceed DRAM"},
+        "other_path_fit": other_fit,
+        "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
@@ -418,6 +486,7 @@ def main():
     ap.add_argument("--impl", choices=["csx", "reference"], default="csx")
     ap.add_argument("--path", choices=["auto", "stream", "moment"], default="auto")
     ap.add_argument("--nconf", type=int, default=SCAN["nconf"])
+    ap.add_argument("--threads", type=int, default=0, help="fit CTA size (0 = automatic)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -56,7 +56,8 @@ extern "C" {
 #define CSX_FIT_NONPHYSICAL 2   /* non-finite likelihood at the start (e.g. singular A^T N^-1 A) */
 #define CSX_FIT_LINESEARCH 3    /* no acceptable step from the current point */
 
-/* likelihood evaluation inside the fit */
+/* likelihood evaluation inside the fit (AUTO: MOMENT for homogeneous or separable noise with the
+ * adjoint gradient, STREAM otherwise) */
 #define CSX_PATH_AUTO 0
 #define CSX_PATH_STREAM 1  /* per pixel, any noise model */
 #define CSX_PATH_MOMENT 2  /* per cell of equal (l_d, l_T, l_s); separable/homogeneous noise */

@@ -8,10 +8,50 @@
 #include <numeric>
 #include <string>
 #include <vector>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 
 #include "csx_host.h"
 
 namespace csx {
+
+// ------------------------------------------------------------------------------ tracing --------
+// CSX_TRACE=1 in the environment: every traced span synchronises its stream and prints its GPU
+// time (CUDA events) and host time to stderr. Off by default; diagnostic only.
+static bool trace_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("CSX_TRACE");
+    return e && *e && *e != '0';
+  }();
+  return on;
+}
+
+struct TraceSpan {
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  std::chrono::steady_clock::time_point t0;
+  TraceSpan(const char* n, cudaStream_t st) : name(n), s(st) {
+    if (!trace_on()) return;
+    t0 = std::chrono::steady_clock::now();
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  ~TraceSpan() {
+    if (!a) return;
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double host =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::fprintf(stderr, "csx trace: %-24s gpu %9.3f ms  host %9.3f ms\n", name, ms, host);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
 
 // ------------------------------------------------------------------------------ errors ---------
 static thread_local std::string g_err;
@@ -297,7 +337,9 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   if (o.lower[1] <= 0.f) return fail(CSX_EINVAL, "T_d lower bound must be > 0");
   if (o.grad_mode == CSX_GRAD_FD && !(o.fd_step > 0)) return fail(CSX_EINVAL, "fd_step must be > 0");
   int path = o.path;
-  if (path == CSX_PATH_AUTO) path = CSX_PATH_STREAM;
+  if (path == CSX_PATH_AUTO)
+    path = (sky->noise_kind != CSX_NOISE_PERPIXEL && o.grad_mode == CSX_GRAD_ADJOINT) ? CSX_PATH_MOMENT
+                                                                                     : CSX_PATH_STREAM;
   if (path != CSX_PATH_MOMENT && path != CSX_PATH_STREAM) return fail(CSX_EINVAL, "unknown path");
   if (path == CSX_PATH_MOMENT && sky->noise_kind == CSX_NOISE_PERPIXEL)
     return fail(CSX_EINVAL, "the moment path needs homogeneous or separable noise");
@@ -343,16 +385,20 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
     coffs = perm + (size_t)nconf * per;
     ncell = coffs + (size_t)nconf * (per + 1);
     int* Kdev = ncell + nconf;
-    CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
-    if ((rc = launch_cells(npix, nconf, labels, Kdev, perm, coffs, ncell, s))) return rc;
-    CSX_CUDA(cudaMemcpyAsync(ncell_h.data(), ncell, (size_t)nconf * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CSX_CUDA(cudaStreamSynchronize(s));
+    {
+      TraceSpan tr("fit: cells", s);
+      CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+      if ((rc = launch_cells(npix, nconf, labels, Kdev, perm, coffs, ncell, s))) return rc;
+      CSX_CUDA(cudaMemcpyAsync(ncell_h.data(), ncell, (size_t)nconf * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CSX_CUDA(cudaStreamSynchronize(s));
+    }
     for (int c = 0; c < nconf; ++c) {
       if (ncell_h[c] < 0) return fail(CSX_ELABEL, "configuration " + std::to_string(c) + " has a label outside [0, K_j)");
       ncell_max = std::max(ncell_max, ncell_h[c]);
     }
   }
 
+  TraceSpan trh("fit: host prep + copies", s);
   // largest-first queue order (longest processing time first)
   std::vector<int> order((size_t)nprob);
   std::iota(order.begin(), order.end(), 0);
@@ -419,6 +465,7 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
     a.xtol[j] = o.xtol[j];
   }
   a.fd_step = o.fd_step;
+  TraceSpan tr("fit: kernel", s);
   return launch_fit(a, o.threads, grid, s);
 }
 
@@ -481,6 +528,7 @@ int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const
   a.sigma2 = sigma2;
   a.r_sys = r_sys;
   a.metrics = metrics;
+  TraceSpan tr("reconstruct: kernel", s);
   return launch_recon(a, s);
 }
 

@@ -260,6 +260,17 @@ __device__ __forceinline__ void load_pixel(const float* __restrict__ p, float (&
 }
 
 // ---------------------------------------------------------------------------------------------
+// Asynchronous 4-byte global -> shared copies (cp.async, L1-allocating); a thread waits for its
+// own copies only.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------------------
 // Block reductions: every thread of the block receives the total. `sbuf` holds NT/32 values.
 // ---------------------------------------------------------------------------------------------
 template <typename T>

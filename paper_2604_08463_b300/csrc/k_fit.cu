@@ -26,7 +26,7 @@
 
 namespace csx {
 
-constexpr int SMEM_P = 2048;   // parameter vectors up to this length accumulate in shared memory
+constexpr int SMEM_P = 1024;   // parameter vectors up to this length accumulate in shared memory
 constexpr int MAXM = 16;       // maximum L-BFGS memory
 
 struct Ctx {
@@ -226,7 +226,8 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
   float nsum = 0.f;
 #pragma unroll
   for (int f = 0; f < 15; ++f) nsum += nb[f];
-  float* row = c.smem + threadIdx.x;  // row[k * NT]: T1 k = 0..14, T2 15..29, B 30..74
+  float* row = c.smem + threadIdx.x;            // row[k * NT]: N A_1 (k = 0..14), N A_2 (15..29)
+  float* ms = c.smem + 30 * NT + threadIdx.x;   // ms[e * NT]: the cell's 171 staged moments
   double acc = 0.0;
   for (int cell = threadIdx.x; cell < c.ncell; cell += NT) {
     const int kd = c.trip[cell], kt = c.trip[c.ncell + cell], ks = c.trip[2 * c.ncell + cell];
@@ -237,8 +238,16 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const float* pdr = c.tabr + kd * NB;
     const float* btr = c.tabr + (c.Kd + kt) * NB;
     const float* ssr = c.tabr + (c.Kd + 2 * c.KT + ks) * NB;
-    const float* Mc = c.mom + cell;
-    const long long st = c.ncell;
+    {
+      // stage the cell's moments into this thread's shared column: all 171 copies in flight at
+      // once, consumed after the table pass below (the cell's previous use of the column has
+      // completed: every read of it precedes this point in program order)
+      const float* Mc = c.mom + cell;
+      const long long st = c.ncell;
+#pragma unroll 19
+      for (int e = 0; e < NM; ++e) cp_async4(ms + e * NT, Mc + e * st);
+      cp_async_commit();
+    }
     // M = A^T N A and Z = A_r^T N A
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
     float z10 = 0.f, z11 = 0.f, z12 = 0.f, z20 = 0.f, z21 = 0.f, z22 = 0.f;
@@ -262,6 +271,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       z21 = fmaf(r2, t1, z21);
       z22 = fmaf(r2, t2, z22);
     }
+    cp_async_wait_all();
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
       acc += (double)nan_f();
@@ -292,7 +302,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = Mc[mom_index(f, 15 + k) * st];
+        C[k] = ms[mom_index(f, 15 + k) * NT];
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -305,35 +315,40 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
         }
       }
     }
-    // B = R N A row by row (kept in shared memory), A^T N R N A and tr(N R)
+    // B = R N A row by row, A^T N R N A, tr(N R), and the gradient part carried by B: with
+    // E = U + C Z + B - A Psi, the B term of E M^-1 in band i is sum_l B[i][l] M^-1[l][k]
     float trNR = 0.f;
     float AtRA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float gbd = 0.f, gtd = 0.f, gbs = 0.f;
 #pragma unroll 1
     for (int i = 0; i < 15; ++i) {
       float b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
       for (int j = 0; j < 15; ++j) {
-        const float s = (j >= i) ? Mc[mom_index(i, j) * st] : Mc[mom_index(j, i) * st];
+        const float s = (j >= i) ? ms[mom_index(i, j) * NT] : ms[mom_index(j, i) * NT];
         b0 = fmaf(s, nb[j], b0);
         b1 = fmaf(s, row[j * NT], b1);
         b2 = fmaf(s, row[(15 + j) * NT], b2);
         if (j == i) trNR = fmaf(nb[j], s, trNR);
       }
-      row[(30 + i) * NT] = b0;
-      row[(45 + i) * NT] = b1;
-      row[(60 + i) * NT] = b2;
       const float na[3] = {nb[i], row[i * NT], row[(15 + i) * NT]};
       const float bf[3] = {b0, b1, b2};
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int l = 0; l < 3; ++l) AtRA[k][l] = fmaf(na[k], bf[l], AtRA[k][l]);
+      const float fb1 = b0 * v[0][1] + b1 * v[1][1] + b2 * v[2][1];
+      const float fb2 = b0 * v[0][2] + b1 * v[1][2] + b2 * v[2][2];
+      const float t1 = fb1 * na[1];
+      gbd = fmaf(t1, a.bands.lnd[i], gbd);
+      gtd = fmaf(t1, dt[i], gtd);
+      gbs = fmaf(fb2 * na[2], a.bands.lns[i], gbs);
     }
     float Q[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = Mc[mom_index(15 + k, 15 + l) * st];
+      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = ms[mom_index(15 + k, 15 + l) * NT];
     float chi = 2.f * tdc + trNR;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -356,23 +371,21 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
         for (int l = 0; l < 3; ++l) Psi[m][l] = v[m][0] * H[0][l] + v[m][1] * H[1][l] + v[m][2] * H[2][l];
     }
-    float gbd = 0.f, gtd = 0.f, gbs = 0.f;
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
       const float ar[3] = {1.f, pdr[f] * btr[f], ssr[f]};
-      const float bf[3] = {row[(30 + f) * NT], row[(45 + f) * NT], row[(60 + f) * NT]};
       float D[3], C[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = Mc[mom_index(f, 15 + k) * st];
+        C[k] = ms[mom_index(f, 15 + k) * NT];
       }
       float E[3];
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
         const float U = D[0] * W1[0][l] + D[1] * W1[1][l] + D[2] * W1[2][l];
-        const float X = C[0] * Z[0][l] + C[1] * Z[1][l] + C[2] * Z[2][l] + bf[l];
+        const float X = C[0] * Z[0][l] + C[1] * Z[1][l] + C[2] * Z[2][l];  // + B: added above
         E[l] = U + X - fmaf(a2, Psi[2][l], fmaf(a1, Psi[1][l], Psi[0][l]));
       }
       const float F1 = E[0] * v[0][1] + E[1] * v[1][1] + E[2] * v[2][1];
@@ -654,10 +667,14 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         break;
       }
     }
-    if (it > 0 && stepn <= 1.f && last_step <= 1.f) {
-      if (PATH == CSX_PATH_MOMENT && recentres < 6) {
-        // The moment form rounds in proportion to the distance from the reference point:
-        // converge again about the current point unless it is already close.
+    const bool near_opt = recentres == 0 && stepn <= 100.f && last_step <= 100.f;
+    const bool at_opt = recentres < 6 && stepn <= 1.f && last_step <= 1.f;
+    if (PATH == CSX_PATH_MOMENT && it > 0 && (near_opt || at_opt)) {
+      {
+        // The moment form rounds in proportion to the distance from the reference point: once the
+        // steps are within 100 tolerances of the optimum (first time), and again at convergence,
+        // move the reference here unless it is already close, so that the last iterations run on
+        // precise values. Each move costs one pass over the pixels.
         float dref = 0.f;
         for (int i = tid; i < P; i += NT)
           dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
@@ -675,6 +692,8 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
           continue;
         }
       }
+    }
+    if (it > 0 && stepn <= 1.f && last_step <= 1.f) {
       status = CSX_FIT_CONVERGED;
       break;
     }
@@ -874,9 +893,9 @@ int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path
 
 template <int NT, int PATH>
 constexpr size_t fit_dyn_smem() {
-  // build staging (32 pixel rows per warp) or, during evaluations, 75 floats per thread
+  // build staging (32 pixel rows per warp) or, during evaluations, 30 + 171 floats per thread
   constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
-  constexpr size_t rows = (size_t)75 * NT;
+  constexpr size_t rows = (size_t)(30 + NM) * NT;
   return PATH == CSX_PATH_MOMENT ? (build > rows ? build : rows) * sizeof(float) : 0;
 }
 
@@ -912,30 +931,41 @@ static int launch_one(const FitArgs& a, int grid, cudaStream_t s) {
   return CSX_OK;
 }
 
+// CTA size: the moment path runs 128-thread CTAs by default (two problems per SM overlap their
+// barriers), the streaming path 256; `threads` (128 or 256) overrides it for the moment path.
+static int fit_threads(int threads, int path) {
+  if (path != CSX_PATH_MOMENT) return 256;
+  return threads == 256 ? 256 : 128;
+}
+
 int fit_grid(int threads, int path, int grad_mode, int* grid) {
-  (void)threads;
-  if (path == CSX_PATH_MOMENT) return occupancy_grid<256, CSX_PATH_MOMENT, CSX_GRAD_ADJOINT, CSX_NOISE_SEPARABLE>(grid);
-  if (grad_mode == CSX_GRAD_FD) return occupancy_grid<256, CSX_PATH_STREAM, CSX_GRAD_FD, CSX_NOISE_SEPARABLE>(grid);
-  return occupancy_grid<256, CSX_PATH_STREAM, CSX_GRAD_ADJOINT, CSX_NOISE_SEPARABLE>(grid);
+  constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT, FD = CSX_GRAD_FD;
+  constexpr int SE = CSX_NOISE_SEPARABLE;
+  if (path == M)
+    return fit_threads(threads, path) == 128 ? occupancy_grid<128, M, AD, SE>(grid)
+                                             : occupancy_grid<256, M, AD, SE>(grid);
+  if (grad_mode == FD) return occupancy_grid<256, ST, FD, SE>(grid);
+  return occupancy_grid<256, ST, AD, SE>(grid);
 }
 
 int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s) {
-  (void)threads;
   if (a.nprob == 0) return CSX_OK;
   CSX_CUDA(cudaMemsetAsync(a.head, 0, sizeof(int), s));
-  constexpr int NT = 256;
   constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT, FD = CSX_GRAD_FD;
   constexpr int HO = CSX_NOISE_HOMOGENEOUS, SE = CSX_NOISE_SEPARABLE, PP = CSX_NOISE_PERPIXEL;
   if (a.path == M) {
-    return a.noise_kind == SE ? launch_one<NT, M, AD, SE>(a, grid, s) : launch_one<NT, M, AD, HO>(a, grid, s);
+    const bool sep = a.noise_kind == SE;
+    if (fit_threads(threads, M) == 128)
+      return sep ? launch_one<128, M, AD, SE>(a, grid, s) : launch_one<128, M, AD, HO>(a, grid, s);
+    return sep ? launch_one<256, M, AD, SE>(a, grid, s) : launch_one<256, M, AD, HO>(a, grid, s);
   } else if (a.grad_mode == FD) {
-    if (a.noise_kind == SE) return launch_one<NT, ST, FD, SE>(a, grid, s);
-    if (a.noise_kind == HO) return launch_one<NT, ST, FD, HO>(a, grid, s);
-    return launch_one<NT, ST, FD, PP>(a, grid, s);
+    if (a.noise_kind == SE) return launch_one<256, ST, FD, SE>(a, grid, s);
+    if (a.noise_kind == HO) return launch_one<256, ST, FD, HO>(a, grid, s);
+    return launch_one<256, ST, FD, PP>(a, grid, s);
   }
-  if (a.noise_kind == SE) return launch_one<NT, ST, AD, SE>(a, grid, s);
-  if (a.noise_kind == HO) return launch_one<NT, ST, AD, HO>(a, grid, s);
-  return launch_one<NT, ST, AD, PP>(a, grid, s);
+  if (a.noise_kind == SE) return launch_one<256, ST, AD, SE>(a, grid, s);
+  if (a.noise_kind == HO) return launch_one<256, ST, AD, HO>(a, grid, s);
+  return launch_one<256, ST, AD, PP>(a, grid, s);
 }
 
 }  // namespace csx

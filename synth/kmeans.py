@@ -60,6 +60,31 @@ def spherical_kmeans(vec: np.ndarray, k: int, seed: int, max_iter: int = 30) -> 
     return remap[labels].astype(np.int32)
 
 
+def _disk_path(key: str, n: int, k: int):
+    d = os.environ.get("CSX_KMEANS_CACHE")
+    if not d or not key:
+        return None
+    return os.path.join(d, "km_%s_%d_%d.npy" % (key, n, k))
+
+
+def _from_disk(key, n, k):
+    p = _disk_path(key, n, k)
+    if p and os.path.exists(p):
+        lab = np.load(p).astype(np.int32)
+        if lab.shape == (n,):
+            return lab
+    return None
+
+
+def _to_disk(key, n, k, lab):
+    p = _disk_path(key, n, k)
+    if p:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + ".%d.tmp.npy" % os.getpid()
+        np.save(tmp, lab.astype(np.int16 if lab.max() < 32767 else np.int32))
+        os.replace(tmp, p)
+
+
 def patch_labels(vec: np.ndarray, k: int, key: str = "") -> np.ndarray:
     """Labels for K patches on the pixel set `vec`, seeded by K (seed 100 + K), memoised.
 
@@ -76,7 +101,16 @@ def _worker(args):
 
 
 def many_patch_labels(vec: np.ndarray, ks, key: str = "", processes: int | None = None):
-    """Labelings for every distinct K in `ks` (dict K -> labels), computed in a spawn pool."""
+    """Labelings for every distinct K in `ks` (dict K -> labels), computed in a spawn pool.
+
+    With CSX_KMEANS_CACHE set to a directory, labelings are also read from / written to disk there
+    (keyed by pixel-set name, pixel count and K; the algorithm is deterministic)."""
+    n = vec.shape[0]
+    for k in {int(k) for k in ks}:
+        if (key, n, k) not in _CACHE:
+            lab = _from_disk(key, n, k)
+            if lab is not None:
+                _CACHE[(key, n, k)] = lab
     todo = sorted({int(k) for k in ks if (key, vec.shape[0], int(k)) not in _CACHE}, reverse=True)
     if todo:
         nproc = processes or min(len(todo), len(os.sched_getaffinity(0)))
@@ -86,7 +120,9 @@ def many_patch_labels(vec: np.ndarray, ks, key: str = "", processes: int | None 
             with mp.get_context("spawn").Pool(nproc) as pool:
                 for k, lab in pool.imap_unordered(_worker, [(vec, k) for k in todo]):
                     _CACHE[(key, vec.shape[0], k)] = lab
+                    _to_disk(key, n, k, lab)
         else:
             for k in todo:
                 _CACHE[(key, vec.shape[0], k)] = spherical_kmeans(vec, k, seed=100 + k)
+                _to_disk(key, n, k, _CACHE[(key, n, k)])
     return {int(k): _CACHE[(key, vec.shape[0], int(k))] for k in ks}
