@@ -160,6 +160,24 @@ int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* lab
                       float* grad, void* stream);
 
 /*
+ * csx_spectral_grad without any device allocation. The paper has no counterpart: this is an
+ * interface for callers that cannot let a library call cudaMalloc -- applications whose device
+ * memory belongs to their own pool allocator (an allocation behind its back can fail or fragment
+ * the pool), and latency-critical loops with a fixed memory budget.
+ * Same arguments and results as csx_spectral_grad, except that L must not be NULL. The only
+ * scratch, the SED tables, lives in a static device array of 2^20 floats (4 MiB) that stays
+ * resident on every device that loads the library until the process exits;
+ * nprob x (K_d + 2 K_T + K_s) x 16 must not exceed 2^20, otherwise the call returns CSX_EINVAL and
+ * enqueues nothing. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture begins. All calls on a
+ * device share the array and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (for example on different streams) race and must be serialised by the caller.
+ */
+int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                              const int32_t K[3], int32_t nprob, const float* beta, double* L,
+                              float* grad, void* stream);
+
+/*
  * Cells of each configuration: pixels sorted stably by (l_d, l_T, l_s) (Sec. 2.2-2.3).
  *   labels   device int32 [nconf][3][npix];  K host int32 [nconf][3]
  *   perm     device int32 [nconf][npix]      sorted pixel indices

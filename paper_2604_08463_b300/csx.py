@@ -22,8 +22,8 @@ STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search"}
 M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
-           "csx_spectral_like", "csx_spectral_grad", "csx_build_cells", "csx_fit_batch",
-           "csx_reconstruct", "csx_select"]
+           "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_noalloc",
+           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select"]
 
 
 class CsxError(RuntimeError):
@@ -68,6 +68,8 @@ def lib():
         L.csx_mixing.argtypes = [POINTER(CModel), i32, vp, vp, vp, vp]
         L.csx_spectral_like.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp]
         L.csx_spectral_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp, vp]
+        L.csx_spectral_grad_noalloc.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp,
+                                                vp, vp, vp]
         L.csx_build_cells.argtypes = [i32, i32, vp, pi32, vp, vp, vp, vp]
         L.csx_fit_batch.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32,
                                     POINTER(CFitOpts), vp, vp, vp, vp, vp, vp, vp]
@@ -197,6 +199,18 @@ def spectral_grad(model: Model, sky: Sky, labels, K, beta):
     _check(lib().csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
                                    beta.shape[0], _ptr(beta), _ptr(L), _ptr(g), _stream()))
     return L, g
+
+
+def spectral_grad_noalloc(model: Model, sky: Sky, labels, K, beta, L, grad):
+    """csx_spectral_grad_noalloc into caller-provided outputs L [nprob] float64 and grad [nprob, P]
+    float32: the library allocates no device memory for this call (for callers whose device memory
+    is owned by their own allocator or budget)."""
+    K, Kp = _host_i32(K)
+    beta = beta.to(torch.float32).contiguous()
+    _check(lib().csx_spectral_grad_noalloc(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels),
+                                           Kp, beta.shape[0], _ptr(beta), _ptr(L), _ptr(grad),
+                                           _stream()))
+    return L, grad
 
 
 def build_cells(labels: torch.Tensor, K):
