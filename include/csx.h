@@ -20,6 +20,9 @@
  *     in time on different streams.
  *   - Band axis: every per-pixel vector has 16 float slots; bands nfreq..15 must hold zeros.
  *   - Data d: float32 [nreal][npix][2][16], Stokes Q then U: one 128-byte line per pixel.
+ *   - Alignment: d, ninv_pix and d_fg must be 16-byte aligned (pixel rows are read as 16-byte
+ *     vectors and staged by tensor copies); every other array its element size (4 bytes, 8 for
+ *     double). A misaligned pointer is refused with CSX_EINVAL before anything is enqueued.
  *   - Patch labels: int32 [3][npix] per configuration (beta_d, T_d, beta_s labelings), values in
  *     [0, K_j). Labels out of range make the affected problem's likelihood NaN (spectral calls,
  *     reconstruction) or the fit call return CSX_ELABEL.
@@ -39,7 +42,7 @@ extern "C" {
 
 /* return codes */
 #define CSX_OK 0
-#define CSX_EINVAL (-1)   /* null pointer, bad size or option */
+#define CSX_EINVAL (-1)   /* null or misaligned pointer, bad size or option */
 #define CSX_ECUDA (-2)    /* a CUDA runtime call failed */
 #define CSX_ENOMEM (-3)   /* scratch allocation failed */
 #define CSX_ETIMEOUT (-4) /* a bounded device wait gave up */
@@ -93,10 +96,10 @@ typedef struct csx_sky {
   int32_t nreal;                       /* realizations stored in d */
   int32_t noise_kind;                  /* CSX_NOISE_* */
   int32_t reserved;
-  const float* d;                      /* device [nreal][npix][2][16] */
+  const float* d;                      /* device [nreal][npix][2][16], 16-byte aligned */
   float ninv_band[CSX_MAX_BANDS];      /* host values: 1/sigma_f^2 (HOMOGENEOUS, SEPARABLE) */
   const float* w;                      /* device [npix] hit-count weights (SEPARABLE), else NULL */
-  const float* ninv_pix;               /* device [npix][16] (PERPIXEL), else NULL */
+  const float* ninv_pix;               /* device [npix][16] (PERPIXEL), 16-byte aligned, else NULL */
 } csx_sky;
 
 /* Options of csx_fit_batch. csx_fit_defaults() fills the values quoted here. */

@@ -161,8 +161,26 @@ static int check_model(const csx_model* m) {
   return CSX_OK;
 }
 
+int check_align(const void* p, size_t align, const char* what) {
+  if (p && (reinterpret_cast<uintptr_t>(p) % align) != 0)
+    return fail(CSX_EINVAL, std::string(what) + " must be " + std::to_string(align) +
+                                "-byte aligned");
+  return CSX_OK;
+}
+
+#define CSX_ALIGN(p, n)                                    \
+  do {                                                     \
+    const int rc_ = check_align((p), (n), #p);             \
+    if (rc_) return rc_;                                   \
+  } while (0)
+
 static int check_sky(const csx_sky* s, int nfreq) {
   if (!s) return fail(CSX_EINVAL, "sky is NULL");
+  // pixel rows are read as 16-byte vectors (and staged by tensor copies): 16-byte alignment
+  int rc;
+  if ((rc = check_align(s->d, 16, "sky->d")) || (rc = check_align(s->ninv_pix, 16, "sky->ninv_pix")) ||
+      (rc = check_align(s->w, 4, "sky->w")))
+    return rc;
   if (s->npix < 0 || s->nreal < 0) return fail(CSX_EINVAL, "npix and nreal must be >= 0");
   if (s->npix > 0 && s->nreal > 0 && !s->d) return fail(CSX_EINVAL, "sky->d is NULL");
   if (s->noise_kind < 0 || s->noise_kind > 2) return fail(CSX_EINVAL, "unknown noise_kind");
@@ -228,6 +246,9 @@ int csx_mixing(const csx_model* m, int32_t n, const float* beta, float* A, float
   if (rc) return rc;
   if (n < 0) return fail(CSX_EINVAL, "n must be >= 0");
   if (n > 0 && (!beta || !A)) return fail(CSX_EINVAL, "beta and A must not be NULL");
+  CSX_ALIGN(beta, 4);
+  CSX_ALIGN(A, 4);
+  CSX_ALIGN(dA, 4);
   return launch_mixing(make_bands(*m), n, beta, A, dA, (cudaStream_t)stream);
 }
 
@@ -245,6 +266,10 @@ static int spectral_common(const csx_model* m, const csx_sky* sky, const int32_t
   if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
   if (want_grad && !grad) return fail(CSX_EINVAL, "grad is NULL");
   if (!want_grad && !L) return fail(CSX_EINVAL, "L is NULL");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(beta, 4);
+  CSX_ALIGN(L, 8);
+  CSX_ALIGN(grad, 4);
   cudaStream_t s = (cudaStream_t)stream;
   const int P = K[0] + K[1] + K[2];
   const int rows = K[0] + 2 * K[1] + K[2];
@@ -300,6 +325,10 @@ int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const in
   if (nconf == 0) return CSX_OK;
   if (!K || !perm || !cell_off || !ncell || (npix > 0 && !labels))
     return fail(CSX_EINVAL, "NULL argument");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(perm, 4);
+  CSX_ALIGN(cell_off, 4);
+  CSX_ALIGN(ncell, 4);
   for (int c = 0; c < nconf; ++c) {
     int rc = check_K(K + 3 * c);
     if (rc) return rc;
@@ -326,6 +355,13 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   if (!K || !opts || !beta0 || !beta_out || !L_out || !status || !iters)
     return fail(CSX_EINVAL, "NULL argument");
   if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(beta0, 4);
+  CSX_ALIGN(beta_out, 4);
+  CSX_ALIGN(L_out, 8);
+  CSX_ALIGN(status, 4);
+  CSX_ALIGN(iters, 4);
+  CSX_ALIGN(nevals, 4);
   const csx_fit_opts& o = *opts;
   if (o.history < 1 || o.history > 16) return fail(CSX_EINVAL, "history must be in 1..16");
   if (o.max_iter < 0 || o.max_ls < 1) return fail(CSX_EINVAL, "max_iter >= 0 and max_ls >= 1 required");
@@ -480,6 +516,13 @@ int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const
   if (nprob == 0) return CSX_OK;
   if (!K || !beta) return fail(CSX_EINVAL, "NULL argument");
   if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(beta, 4);
+  CSX_ALIGN(d_fg, 16);
+  CSX_ALIGN(s_hat, 4);
+  CSX_ALIGN(sigma2, 4);
+  CSX_ALIGN(r_sys, 4);
+  CSX_ALIGN(metrics, 8);
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<ProbDesc> probs((size_t)nprob);
   long long poff = 0, toff = 0;
@@ -536,6 +579,9 @@ int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot
                void* stream) {
   if (nconf < 1 || nreal < 1) return fail(CSX_EINVAL, "nconf and nreal must be >= 1");
   if (!metrics || !vtot || !best) return fail(CSX_EINVAL, "NULL argument");
+  CSX_ALIGN(metrics, 8);
+  CSX_ALIGN(vtot, 8);
+  CSX_ALIGN(best, 4);
   return launch_select(nconf, nreal, metrics, vtot, best, (cudaStream_t)stream);
 }
 

@@ -271,6 +271,41 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------------------------
+// Scatter-add of per-lane values into acc[key], combined over runs of equal keys in consecutive
+// lanes: pixels in ring order fall into a patch in long runs, so a warp mostly carries one to three
+// distinct keys and issues one atomic per run instead of 32 atomics on the same address. A
+// segmented inclusive scan (shuffles) leaves each run's total in its last lane. Every lane of the
+// warp must call it; lanes with key < 0 add nothing. Three keys are scanned together.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_run_add3(float* acc0, int k0, float v0, float* acc1, int k1,
+                                              float v1, float* acc2, int k2, float v2) {
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = (2u << lane) - 1u;  // lanes 0..lane (lane 31: all bits, by wrap-around)
+  const int p0 = __shfl_up_sync(full, k0, 1), p1 = __shfl_up_sync(full, k1, 1),
+            p2 = __shfl_up_sync(full, k2, 1);
+  const unsigned h0 = __ballot_sync(full, lane == 0 || k0 != p0);
+  const unsigned h1 = __ballot_sync(full, lane == 0 || k1 != p1);
+  const unsigned h2 = __ballot_sync(full, lane == 0 || k2 != p2);
+  const int s0 = 31 - __clz(h0 & upto), s1 = 31 - __clz(h1 & upto), s2 = 31 - __clz(h2 & upto);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float t0 = __shfl_up_sync(full, v0, d), t1 = __shfl_up_sync(full, v1, d),
+                t2 = __shfl_up_sync(full, v2, d);
+    if (lane - d >= s0) v0 += t0;
+    if (lane - d >= s1) v1 += t1;
+    if (lane - d >= s2) v2 += t2;
+  }
+  // a run ends in lane 31 or before the next head
+  const unsigned after = (lane == 31) ? 0xffffffffu : ((h0 >> (lane + 1)) & 1u) * 0x1u |
+                                                        (((h1 >> (lane + 1)) & 1u) << 1) |
+                                                        (((h2 >> (lane + 1)) & 1u) << 2);
+  if (k0 >= 0 && (after & 1u)) atomicAdd(acc0 + k0, v0);
+  if (k1 >= 0 && (after & 2u)) atomicAdd(acc1 + k1, v1);
+  if (k2 >= 0 && (after & 4u)) atomicAdd(acc2 + k2, v2);
+}
+
+// ---------------------------------------------------------------------------------------------
 // Block reductions: every thread of the block receives the total. `sbuf` holds NT/32 values.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
@@ -338,6 +373,164 @@ __device__ __forceinline__ T block_min(T v, T* sbuf) {
   __syncthreads();
   T t = ((threadIdx.x & 31) < NT / 32) ? sbuf[threadIdx.x & 31] : sbuf[0];
   return warp_min(t);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Separable noise N_p^-1 = w_p diag(n) (homogeneous: w_p = 1). The Gram-Schmidt factors of mgs3
+// do not depend on w_p, so every pixel of a cell (equal labels) shares them, and in that basis the
+// likelihood term of Eq. 3 is a sum of squared projections (no residual needs forming):
+//   b^T M^-1 b = w_p sum_k <e_k, d>^2 / <c_k, c_k>_n,   e = n (1, c1, c2),
+// while the gradient of Sec. 3.3.1 needs, per parameter with dA/dbeta = column j scaled by l,
+//   r^T N dA s_hat = w_p s_hat_j (<v, d> - sum_k s_hat_k <v, a_k>),   v = n a_j l,  a = (1, A_d, A_s).
+// run_scalars: the per-cell scalars (1/<c_k,c_k>, mu1, mu2, nu and the nine <v, a_k>) of one cell,
+// by one thread, written as 16 floats: i0, i1, i2, mu1, mu2, nu, u[0..8], 0.
+// ---------------------------------------------------------------------------------------------
+constexpr int NSC = 15;  // i0, i1, i2, mu1, mu2, nu, u[9] with u[3 j + k] = <v_j, a_k>
+
+__device__ __forceinline__ void load_row16(const float* __restrict__ r, float (&x)[NB]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = *reinterpret_cast<const float4*>(r + 4 * k);
+    x[4 * k] = v.x; x[4 * k + 1] = v.y; x[4 * k + 2] = v.z; x[4 * k + 3] = v.w;
+  }
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void run_scalars(const float* __restrict__ pd,
+                                            const float* __restrict__ bt,
+                                            const float* __restrict__ dt,
+                                            const float* __restrict__ ss, const float* nband,
+                                            const Bands& bc, float n0, float* out) {
+  float ad[NB], as[NB];
+  {
+    float p[NB], b[NB];
+    load_row16(pd, p);
+    load_row16(bt, b);
+    load_row16(ss, as);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) ad[f] = p[f] * b[f];
+  }
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    s1 = fmaf(nband[f], ad[f], s1);
+    s2 = fmaf(nband[f], as[f], s2);
+  }
+  const float i0 = 1.f / n0, mu1 = s1 * i0, mu2 = s2 * i0;
+  float n1 = 0.f, x12 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    const float c1 = ad[f] - mu1, w = nband[f] * c1;
+    n1 = fmaf(w, c1, n1);
+    x12 = fmaf(w, as[f], x12);
+  }
+  const float i1 = 1.f / n1, nu = x12 * i1;
+  float n2 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) {
+    const float c2 = fmaf(-nu, ad[f] - mu1, as[f] - mu2);
+    n2 = fmaf(nband[f] * c2, c2, n2);
+  }
+  const float i2 = 1.f / n2;
+  float u[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (GRAD) {
+    float d[NB];
+    load_row16(dt, d);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+      const float nad = nband[f] * ad[f], nas = nband[f] * as[f];
+      const float vb = nad * bc.lnd[f], vt = nad * d[f], vs = nas * bc.lns[f];
+      u[0] += vb; u[1] = fmaf(vb, ad[f], u[1]); u[2] = fmaf(vb, as[f], u[2]);
+      u[3] += vt; u[4] = fmaf(vt, ad[f], u[4]); u[5] = fmaf(vt, as[f], u[5]);
+      u[6] += vs; u[7] = fmaf(vs, ad[f], u[7]); u[8] = fmaf(vs, as[f], u[8]);
+    }
+  }
+  float4* o = reinterpret_cast<float4*>(out);
+  o[0] = make_float4(i0, i1, i2, mu1);
+  o[1] = make_float4(mu2, nu, u[0], u[1]);
+  o[2] = make_float4(u[2], u[3], u[4], u[5]);
+  o[3] = make_float4(u[6], u[7], u[8], 0.f);
+}
+
+__device__ __forceinline__ void load_scalars(const float* __restrict__ src, float (&sc)[NSC]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  const float4 a = s4[0], b = s4[1], c = s4[2], d = s4[3];
+  sc[0] = a.x; sc[1] = a.y; sc[2] = a.z; sc[3] = a.w;
+  sc[4] = b.x; sc[5] = b.y; sc[6] = b.z; sc[7] = b.w;
+  sc[8] = c.x; sc[9] = c.y; sc[10] = c.z; sc[11] = c.w;
+  sc[12] = d.x; sc[13] = d.y; sc[14] = d.z;
+}
+
+// One pixel in its cell's basis (scalars from run_scalars, band vectors rebuilt from the SED
+// table rows): L_p = -b^T M^-1 b summed over Q and U, and (GRAD) its contributions to dL/dbeta_d,
+// dL/dT_d, dL/dbeta_s.
+template <bool GRAD>
+__device__ __forceinline__ float cell_pixel(const float (&dq)[NB], const float (&du)[NB],
+                                            const float* __restrict__ pd,
+                                            const float* __restrict__ bt,
+                                            const float* __restrict__ dt,
+                                            const float* __restrict__ ss, const float* nband,
+                                            const Bands& bc, const float (&sc)[NSC], float w,
+                                            float& gbd, float& gtd, float& gbs) {
+  const float mu1 = sc[3], mu2 = sc[4], nu = sc[5];
+  float t0q = 0.f, t1q = 0.f, t2q = 0.f, t0u = 0.f, t1u = 0.f, t2u = 0.f;
+  float bq = 0.f, tq = 0.f, sq = 0.f, bu = 0.f, tu = 0.f, su = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 p4 = *reinterpret_cast<const float4*>(pd + 4 * k);
+    const float4 b4 = *reinterpret_cast<const float4*>(bt + 4 * k);
+    const float4 s4 = *reinterpret_cast<const float4*>(ss + 4 * k);
+    float4 d4;
+    if (GRAD) d4 = *reinterpret_cast<const float4*>(dt + 4 * k);
+    const float pa[4] = {p4.x, p4.y, p4.z, p4.w}, ba[4] = {b4.x, b4.y, b4.z, b4.w},
+                sa[4] = {s4.x, s4.y, s4.z, s4.w};
+    float da[4] = {0.f, 0.f, 0.f, 0.f};
+    if (GRAD) { da[0] = d4.x; da[1] = d4.y; da[2] = d4.z; da[3] = d4.w; }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int f = 4 * k + c;
+      const float n = nband[f];
+      const float ad = pa[c] * ba[c];
+      const float nad = n * ad, nas = n * sa[c];
+      const float e1 = fmaf(-mu1, n, nad);
+      const float e2 = fmaf(-nu, e1, fmaf(-mu2, n, nas));
+      const float xq = dq[f], xu = du[f];
+      t0q = fmaf(n, xq, t0q);
+      t0u = fmaf(n, xu, t0u);
+      t1q = fmaf(e1, xq, t1q);
+      t1u = fmaf(e1, xu, t1u);
+      t2q = fmaf(e2, xq, t2q);
+      t2u = fmaf(e2, xu, t2u);
+      if (GRAD) {
+        const float vb = nad * bc.lnd[f], vt = nad * da[c], vs = nas * bc.lns[f];
+        bq = fmaf(vb, xq, bq);
+        bu = fmaf(vb, xu, bu);
+        tq = fmaf(vt, xq, tq);
+        tu = fmaf(vt, xu, tu);
+        sq = fmaf(vs, xq, sq);
+        su = fmaf(vs, xu, su);
+      }
+    }
+  }
+  const float i0 = sc[0], i1 = sc[1], i2 = sc[2];
+  if (GRAD) {
+    const float s2q = t2q * i2, s2u = t2u * i2;
+    const float s1q = fmaf(-nu, s2q, t1q * i1), s1u = fmaf(-nu, s2u, t1u * i1);
+    const float s0q = t0q * i0 - mu1 * s1q - mu2 * s2q;
+    const float s0u = t0u * i0 - mu1 * s1u - mu2 * s2u;
+    const float rbq = bq - (s0q * sc[6] + s1q * sc[7] + s2q * sc[8]);
+    const float rbu = bu - (s0u * sc[6] + s1u * sc[7] + s2u * sc[8]);
+    const float rtq = tq - (s0q * sc[9] + s1q * sc[10] + s2q * sc[11]);
+    const float rtu = tu - (s0u * sc[9] + s1u * sc[10] + s2u * sc[11]);
+    const float rsq = sq - (s0q * sc[12] + s1q * sc[13] + s2q * sc[14]);
+    const float rsu = su - (s0u * sc[12] + s1u * sc[13] + s2u * sc[14]);
+    const float m2w = -2.f * w;
+    gbd = m2w * fmaf(s1q, rbq, s1u * rbu);
+    gtd = m2w * fmaf(s1q, rtq, s1u * rtu);
+    gbs = m2w * fmaf(s2q, rsq, s2u * rsu);
+  }
+  return -w * (i0 * fmaf(t0q, t0q, t0u * t0u) + i1 * fmaf(t1q, t1q, t1u * t1u) +
+               i2 * fmaf(t2q, t2q, t2u * t2u));
 }
 
 }  // namespace csx

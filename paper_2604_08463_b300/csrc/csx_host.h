@@ -12,6 +12,8 @@ namespace csx {
 
 // ---- error reporting (thread-local message, negative return codes) ----------------------------
 int fail(int code, const std::string& msg);
+// CSX_EINVAL unless the (device) pointer is a multiple of `align` bytes; NULL passes.
+int check_align(const void* p, size_t align, const char* what);
 int cuda_fail(cudaError_t e, const char* where);
 #define CSX_CUDA(call)                                  \
   do {                                                  \

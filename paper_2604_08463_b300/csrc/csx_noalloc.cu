@@ -71,6 +71,14 @@ extern "C" int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky,
     return fail(CSX_EINVAL, "separable noise needs sky->w");
   if (sky->noise_kind == CSX_NOISE_PERPIXEL && sky->npix > 0 && !sky->ninv_pix)
     return fail(CSX_EINVAL, "per-pixel noise needs sky->ninv_pix");
+  {
+    int rc0;
+    if ((rc0 = check_align(sky->d, 16, "sky->d")) || (rc0 = check_align(sky->ninv_pix, 16, "sky->ninv_pix")) ||
+        (rc0 = check_align(sky->w, 4, "sky->w")) || (rc0 = check_align(labels, 4, "labels")) ||
+        (rc0 = check_align(beta, 4, "beta")) || (rc0 = check_align(L, 8, "L")) ||
+        (rc0 = check_align(grad, 4, "grad")))
+      return rc0;
+  }
   if (sky->noise_kind != CSX_NOISE_PERPIXEL)
     for (int f = 0; f < m->nfreq; ++f)
       if (!(sky->ninv_band[f] >= 0.f) || !std::isfinite(sky->ninv_band[f]))

@@ -26,6 +26,17 @@
 
 namespace csx {
 
+// Build-time tuning switches (the defaults are the measured best on B300):
+//   CSX_FIT_STAGE_MOMENTS  1: a cell's 171 moments are staged into shared memory by cp.async
+//                          before use; 0: read from global memory (L2) where used.
+//   CSX_FIT_MIN_BLOCKS     minimum resident 128-thread moment-path CTAs per SM asked of ptxas.
+#ifndef CSX_FIT_STAGE_MOMENTS
+#define CSX_FIT_STAGE_MOMENTS 0
+#endif
+#ifndef CSX_FIT_MIN_BLOCKS
+#define CSX_FIT_MIN_BLOCKS 4
+#endif
+
 constexpr int SMEM_P = 1024;   // parameter vectors up to this length accumulate in shared memory
 constexpr int MAXM = 16;       // maximum L-BFGS memory
 
@@ -75,14 +86,15 @@ __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, floa
 // partial sums are flushed every 16 pixels to bound FP32 rounding growth. Also sum w d^T n d.
 constexpr int NM = 171;          // stored moment entries per cell
 constexpr int VROW = 44;         // shared floats per pixel: v_Q[20], v_U[20], w (16-byte rows)
-constexpr int BUILD_SMEM_PER_WARP = 32 * VROW;
+constexpr int BUILD_SMEM_PER_WARP = 32 * VROW + 32;  // pixel rows + the cell's basis
 
 __device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
 
 template <int NT, bool SEP>
 __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* sv = smem + warp * BUILD_SMEM_PER_WARP;
+  float* sv = smem + warp * BUILD_SMEM_PER_WARP;  // 32 pixel rows
+  float* sb = sv + 32 * VROW;                      // the cell's basis c1[16], c2[16]
   const int grp = lane / 15, blk = lane % 15;
   // upper-triangle 4x4 blocks of a 5x5 block grid: (ba, bb), ba <= bb
   int ba = 0, rem = blk;
@@ -97,15 +109,33 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
     const int i0 = c.coff[cell], i1 = c.coff[cell + 1];
     const int px0 = c.perm[i0];
     const int kd = c.lab[px0], kt = c.lab[c.npix + px0], ks = c.lab[2 * c.npix + px0];
-    float ad[NB], as[NB], c1[NB], c2[NB], nn[NB];
-#pragma unroll
-    for (int f = 0; f < NB; ++f) {
-      ad[f] = c.tabr[kd * NB + f] * c.tabr[(c.Kd + kt) * NB + f];
-      as[f] = c.tabr[(c.Kd + 2 * c.KT + ks) * NB + f];
-      nn[f] = nb[f];
-    }
+    // The cell's N-weighted Gram-Schmidt basis (the steps of mgs3), one band per lane; lanes
+    // 16..31 carry zero weight. c1, c2 go to the warp's basis slot for the pixel phase.
     Mgs3 g;
-    const bool okb = mgs3(nn, ad, as, c1, c2, g);
+    bool okb;
+    {
+      const int f = lane & 15;
+      const float nf = (lane < 16) ? nb[f] : 0.f;
+      const float adf = c.tabr[kd * NB + f] * c.tabr[(c.Kd + kt) * NB + f];
+      const float asf = c.tabr[(c.Kd + 2 * c.KT + ks) * NB + f];
+      const float n0 = warp_sum(nf), s1 = warp_sum(nf * adf), s2 = warp_sum(nf * asf);
+      g.i0 = 1.f / n0;
+      g.mu1 = s1 * g.i0;
+      g.mu2 = s2 * g.i0;
+      const float c1f = adf - g.mu1;
+      const float n1 = warp_sum(nf * c1f * c1f), x12 = warp_sum(nf * c1f * asf);
+      g.i1 = 1.f / n1;
+      g.nu = x12 * g.i1;
+      const float c2f = fmaf(-g.nu, c1f, asf - g.mu2);
+      const float n2 = warp_sum(nf * c2f * c2f);
+      g.i2 = 1.f / n2;
+      okb = (n0 > 0.f) && (n1 > 0.f) && (n2 > 0.f);
+      if (lane < 16) {
+        sb[f] = c1f;
+        sb[16 + f] = c2f;
+      }
+      __syncwarp();
+    }
     float acc[16], tot[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) acc[k] = tot[k] = 0.f;
@@ -122,12 +152,13 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
           const float nq = nb[f] * dq[f], nu = nb[f] * du[f];
+          const float c1 = sb[f], c2 = sb[16 + f];
           tq0 += nq;
-          tq1 = fmaf(nq, c1[f], tq1);
-          tq2 = fmaf(nq, c2[f], tq2);
+          tq1 = fmaf(nq, c1, tq1);
+          tq2 = fmaf(nq, c2, tq2);
           tu0 += nu;
-          tu1 = fmaf(nu, c1[f], tu1);
-          tu2 = fmaf(nu, c2[f], tu2);
+          tu1 = fmaf(nu, c1, tu1);
+          tu2 = fmaf(nu, c2, tu2);
           pd = fmaf(nq, dq[f], fmaf(nu, du[f], pd));
         }
         dnd += (double)(wp * pd);
@@ -135,8 +166,9 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
         tu0 *= g.i0; tu1 *= g.i1; tu2 *= g.i2;
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
-          row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2[f], fmaf(tq1, c1[f], tq0)) : 0.f;
-          row[20 + f] = (f < 15) ? du[f] - fmaf(tu2, c2[f], fmaf(tu1, c1[f], tu0)) : 0.f;
+          const float c1 = sb[f], c2 = sb[16 + f];
+          row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2, fmaf(tq1, c1, tq0)) : 0.f;
+          row[20 + f] = (f < 15) ? du[f] - fmaf(tu2, c2, fmaf(tu1, c1, tu0)) : 0.f;
         }
         // s = R^-1 t (Gram-Schmidt back-substitution)
         const float sq1 = fmaf(-g.nu, tq2, tq1), su1 = fmaf(-g.nu, tu2, tu1);
@@ -227,7 +259,12 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
   for (int f = 0; f < 15; ++f) nsum += nb[f];
   float* row = c.smem + threadIdx.x;            // row[k * NT]: N A_1 (k = 0..14), N A_2 (15..29)
+#if CSX_FIT_STAGE_MOMENTS
   float* ms = c.smem + 30 * NT + threadIdx.x;   // ms[e * NT]: the cell's 171 staged moments
+  constexpr int mst = NT;
+#else
+  const int mst = c.ncell;
+#endif
   double acc = 0.0;
   for (int cell = threadIdx.x; cell < c.ncell; cell += NT) {
     const int kd = c.trip[cell], kt = c.trip[c.ncell + cell], ks = c.trip[2 * c.ncell + cell];
@@ -238,6 +275,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const float* pdr = c.tabr + kd * NB;
     const float* btr = c.tabr + (c.Kd + kt) * NB;
     const float* ssr = c.tabr + (c.Kd + 2 * c.KT + ks) * NB;
+#if CSX_FIT_STAGE_MOMENTS
     {
       // stage the cell's moments into this thread's shared column: all 171 copies in flight at
       // once, consumed after the table pass below (the cell's previous use of the column has
@@ -248,6 +286,9 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       for (int e = 0; e < NM; ++e) cp_async4(ms + e * NT, Mc + e * st);
       cp_async_commit();
     }
+#else
+    const float* ms = c.mom + cell;
+#endif
     // M = A^T N A and Z = A_r^T N A
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
     float z10 = 0.f, z11 = 0.f, z12 = 0.f, z20 = 0.f, z21 = 0.f, z22 = 0.f;
@@ -271,7 +312,9 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       z21 = fmaf(r2, t1, z21);
       z22 = fmaf(r2, t2, z22);
     }
+#if CSX_FIT_STAGE_MOMENTS
     cp_async_wait_all();
+#endif
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
       acc += (double)nan_f();
@@ -302,7 +345,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = ms[mom_index(f, 15 + k) * NT];
+        C[k] = ms[mom_index(f, 15 + k) * mst];
       }
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -325,7 +368,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       float b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
       for (int j = 0; j < 15; ++j) {
-        const float s = (j >= i) ? ms[mom_index(i, j) * NT] : ms[mom_index(j, i) * NT];
+        const float s = (j >= i) ? ms[mom_index(i, j) * mst] : ms[mom_index(j, i) * mst];
         b0 = fmaf(s, nb[j], b0);
         b1 = fmaf(s, row[j * NT], b1);
         b2 = fmaf(s, row[(15 + j) * NT], b2);
@@ -348,7 +391,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = ms[mom_index(15 + k, 15 + l) * NT];
+      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = ms[mom_index(15 + k, 15 + l) * mst];
     float chi = 2.f * tdc + trNR;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -379,7 +422,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = ms[mom_index(f, 15 + k) * NT];
+        C[k] = ms[mom_index(f, 15 + k) * mst];
       }
       float E[3];
 #pragma unroll
@@ -453,49 +496,54 @@ __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_
   const int* ld = c.lab;
   const int* lt = c.lab + c.npix;
   const int* ls = c.lab + 2 * c.npix;
-  for (int p = threadIdx.x; p < c.npix; p += NT) {
-    const int kd = ld[p], kt = lt[p], ks = ls[p];
-    if ((unsigned)kd >= (unsigned)c.Kd || (unsigned)kt >= (unsigned)c.KT ||
-        (unsigned)ks >= (unsigned)c.Ks) {
-      chi += (double)nan_f();
-      continue;
-    }
-    float dq[NB], du[NB], nn[NB];
-    load_pixel(c.d + (long long)p * 2 * NB, dq, du);
-    if (NOISE == CSX_NOISE_PERPIXEL) {
-      const float4* n4 = reinterpret_cast<const float4*>(a.ninv_pix + (long long)p * NB);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float4 v = __ldg(n4 + k);
-        nn[4 * k] = v.x; nn[4 * k + 1] = v.y; nn[4 * k + 2] = v.z; nn[4 * k + 3] = v.w;
-      }
-    } else if (NOISE == CSX_NOISE_SEPARABLE) {
-      const float wp = __ldg(a.w + p);
-#pragma unroll
-      for (int f = 0; f < NB; ++f) nn[f] = wp * nb[f];
-    } else {
-#pragma unroll
-      for (int f = 0; f < NB; ++f) nn[f] = nb[f];
-    }
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count: every lane reaches the warp-wide gradient scatter
+  for (int base = threadIdx.x & ~31; base < c.npix; base += NT) {
+    const int p = base + lane;
+    int kd = -1, kt = -1, ks = -1;
     PixOut o;
-    if (!pixel_eval<GRAD, WANT_H>(dq, du, nn, c.tab + kd * NB, c.tab + (c.Kd + kt) * NB,
-                                  c.tab + (c.Kd + c.KT + kt) * NB,
-                                  c.tab + (c.Kd + 2 * c.KT + ks) * NB, a.bands, o)) {
-      chi += (double)nan_f();
-      continue;
+    o.gbd = o.gtd = o.gbs = o.hbd = o.htd = o.hbs = 0.f;
+    if (p < c.npix) {
+      kd = ld[p];
+      kt = lt[p];
+      ks = ls[p];
+      if ((unsigned)kd >= (unsigned)c.Kd || (unsigned)kt >= (unsigned)c.KT ||
+          (unsigned)ks >= (unsigned)c.Ks) {
+        chi += (double)nan_f();
+        kd = kt = ks = -1;
+      } else {
+        float dq[NB], du[NB], nn[NB];
+        load_pixel(c.d + (long long)p * 2 * NB, dq, du);
+        if (NOISE == CSX_NOISE_PERPIXEL) {
+          const float4* n4 = reinterpret_cast<const float4*>(a.ninv_pix + (long long)p * NB);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 v = __ldg(n4 + k);
+            nn[4 * k] = v.x; nn[4 * k + 1] = v.y; nn[4 * k + 2] = v.z; nn[4 * k + 3] = v.w;
+          }
+        } else if (NOISE == CSX_NOISE_SEPARABLE) {
+          const float wp = __ldg(a.w + p);
+#pragma unroll
+          for (int f = 0; f < NB; ++f) nn[f] = wp * nb[f];
+        } else {
+#pragma unroll
+          for (int f = 0; f < NB; ++f) nn[f] = nb[f];
+        }
+        if (pixel_eval<GRAD, WANT_H>(dq, du, nn, c.tab + kd * NB, c.tab + (c.Kd + kt) * NB,
+                                     c.tab + (c.Kd + c.KT + kt) * NB,
+                                     c.tab + (c.Kd + 2 * c.KT + ks) * NB, a.bands, o)) {
+          chi += (double)o.chi2;
+          dn += (double)o.dnd;
+        } else {
+          chi += (double)nan_f();
+          o.gbd = o.gtd = o.gbs = o.hbd = o.htd = o.hbs = 0.f;
+        }
+      }
     }
-    chi += (double)o.chi2;
-    dn += (double)o.dnd;
-    if (GRAD) {
-      atomicAdd(c.gacc + kd, o.gbd);
-      atomicAdd(c.gacc + c.Kd + kt, o.gtd);
-      atomicAdd(c.gacc + c.Kd + c.KT + ks, o.gbs);
-    }
-    if (WANT_H) {
-      atomicAdd(c.hacc + kd, o.hbd);
-      atomicAdd(c.hacc + c.Kd + kt, o.htd);
-      atomicAdd(c.hacc + c.Kd + c.KT + ks, o.hbs);
-    }
+    if (GRAD)
+      warp_run_add3(c.gacc, kd, o.gbd, c.gacc + c.Kd, kt, o.gtd, c.gacc + c.Kd + c.KT, ks, o.gbs);
+    if (WANT_H)
+      warp_run_add3(c.hacc, kd, o.hbd, c.hacc + c.Kd, kt, o.htd, c.hacc + c.Kd + c.KT, ks, o.hbs);
   }
   block_sum2<NT>(chi, dn, sh.red);
   dnd_out = dn;
@@ -832,7 +880,8 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
 }
 
 template <int NT, int PATH, int GMODE, int NOISE>
-__global__ void __launch_bounds__(NT) k_fit(const __grid_constant__ FitArgs a) {
+__global__ void __launch_bounds__(NT, (PATH == CSX_PATH_MOMENT && NT == 128) ? CSX_FIT_MIN_BLOCKS : 1)
+k_fit(const __grid_constant__ FitArgs a) {
   __shared__ Shared sh;
   __shared__ int s_q;
   extern __shared__ float4 build_smem4[];  // moment build staging (moment path only)
@@ -895,7 +944,7 @@ template <int NT, int PATH>
 constexpr size_t fit_dyn_smem() {
   // build staging (32 pixel rows per warp) or, during evaluations, 30 + 171 floats per thread
   constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
-  constexpr size_t rows = (size_t)(30 + NM) * NT;
+  constexpr size_t rows = (size_t)(30 + (CSX_FIT_STAGE_MOMENTS ? NM : 0)) * NT;
   return PATH == CSX_PATH_MOMENT ? (build > rows ? build : rows) * sizeof(float) : 0;
 }
 

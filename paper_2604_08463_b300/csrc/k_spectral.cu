@@ -1,6 +1,7 @@
 // SED tables, the mixing matrix (Eq. 5) and the streaming likelihood / adjoint-gradient kernel
 // (Eqs. 3-4 over the patches of Sec. 2.2; gradient of Sec. 3.3.1).
 #include "csx_host.h"
+#include "csx_tma.cuh"
 
 namespace csx {
 
@@ -69,110 +70,278 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Streaming likelihood (+ gradient): grid (pixel blocks, problems). Each thread walks pixels with a
-// grid stride, evaluates the residual form in FP32 and accumulates chi2 - d^T N d. Gradients go
-// to a shared-memory copy of the problem's P-vector (one shared atomic per parameter and pixel),
-// flushed to global memory with one atomic per touched parameter and block. Block sums of L are
-// formed in FP64 and added to L[problem] with one FP64 atomic per block.
-// A label outside [0, K_j) or a non-positive-definite A^T N A poisons the problem's L with NaN.
+// Streaming likelihood (+ gradient) of Eqs. 3-4 and Sec. 3.3.1, TMA-staged. Grid (pixel blocks,
+// problems); a CTA takes tiles of TS_NT consecutive pixels of its problem, t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... One thread keeps up to TS_S tiles of d (and of N^-1 for per-pixel
+// noise) in flight with bulk-tensor copies into a ring of shared-memory stages (128-byte swizzled
+// rows, so the per-pixel 16-byte reads are free of bank conflicts); every thread then reads its
+// pixel from shared memory. Labels and hit weights of the next tile are fetched into registers one
+// tile ahead; a stage is refilled after the barrier that follows its last read.
+//
+// Separable / homogeneous noise: the pixels of a tile are split into runs of consecutive pixels
+// with equal labels (within a warp); the Gram-Schmidt scalars of each run are formed once, by one
+// thread, into a shared run table (run_scalars), and every pixel is then evaluated in its run's
+// basis (cell_pixel). Per-pixel noise: each pixel's own Gram-Schmidt solve (pixel_eval).
+//
+// L_p is accumulated in FP32 per thread (a few pixels) and in FP64 across the block, then added to
+// L[problem] with one FP64 atomic per block; gradients go to a shared-memory copy of the problem's
+// P-vector (one atomic per run of equal labels in a warp), flushed with one global atomic per
+// touched parameter and block. A label outside [0, K_j) or a non-positive-definite A^T N A poisons
+// L with NaN. Waits are bounded (about 2 s): on time-out the CTA waits (bounded) for its copies
+// still in flight, poisons L with NaN and returns.
 // ---------------------------------------------------------------------------------------------
-template <int NOISE, bool GRAD, bool SMEM_GRAD>
-__global__ void __launch_bounds__(256) k_spectral(SpecArgs a) {
-  extern __shared__ float sgrad[];
-  __shared__ double sred[8];
-  const int q = blockIdx.y;
-  const float* tab = a.tables + (long long)q * a.rows * NB;
-  const float* dq0 = a.d + (long long)q * a.npix * 2 * NB;
-  float* ggl = GRAD ? a.grad + (long long)q * a.P : nullptr;
-  if (GRAD && SMEM_GRAD) {
-    for (int i = threadIdx.x; i < a.P; i += blockDim.x) sgrad[i] = 0.f;
-    __syncthreads();
+constexpr int TS_NT = 256;                          // threads = pixels per tile
+constexpr int TS_NW = TS_NT / 32;
+constexpr int TS_S = 2;                             // pipeline stages
+constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
+
+template <int NOISE>
+struct TsShape {
+  static constexpr bool RUNS = NOISE != CSX_NOISE_PERPIXEL;
+  static constexpr int DB = TS_NT * 128;                                 // d: [256][2][16] floats
+  static constexpr int NBY = RUNS ? 0 : TS_NT * 64;                      // N^-1: [256][16] floats
+  static constexpr int SB = DB + NBY;                                    // bytes per stage
+  static constexpr int RB = RUNS ? TS_NT * (16 * 4 + 16) : 0;            // run scalars + labels
+  static constexpr size_t smem(int P, bool smem_grad) {
+    return 1024 + (size_t)TS_S * SB + RB + (smem_grad ? (size_t)P * sizeof(float) : 0);
   }
+};
+
+template <int NOISE, bool GRAD, bool SMEM_GRAD>
+__global__ void __launch_bounds__(TS_NT, 2)
+    k_spectral_tma(const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap mn,
+                   const SpecArgs a) {
+  using Sh = TsShape<NOISE>;
+  extern __shared__ __align__(16) unsigned char ts_smem[];
+  __shared__ __align__(8) uint64_t full[TS_S];
+  __shared__ double sred[TS_NW];
+  __shared__ int s_cnt[2][TS_NW];
+  const unsigned off = smem_addr(ts_smem);
+  unsigned char* stage0 = ts_smem + (((off + 1023u) & ~1023u) - off);  // 1024-byte aligned ring
+  float* s_sc = reinterpret_cast<float*>(stage0 + TS_S * Sh::SB);      // [TS_NT][16] run scalars
+  int4* s_trip = reinterpret_cast<int4*>(s_sc + (Sh::RUNS ? TS_NT * 16 : 0));  // [TS_NT] labels
+  float* sgrad = reinterpret_cast<float*>(stage0 + TS_S * Sh::SB + Sh::RB);
+  const int q = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ntile = (a.npix + TS_NT - 1) / TS_NT;
+  const int my = ((int)blockIdx.x < ntile) ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const float* tab = a.tables + (long long)q * a.rows * NB;
+  float* ggl = GRAD ? a.grad + (long long)q * a.P : nullptr;
   float* gacc = SMEM_GRAD ? sgrad : ggl;
+  if (tid == 0) {
+    for (int s = 0; s < TS_S; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+    tma_prefetch_map(&md);
+  }
+  if (GRAD && SMEM_GRAD)
+    for (int i = tid; i < a.P; i += TS_NT) sgrad[i] = 0.f;
+  __syncthreads();
+  auto issue = [&](int j) {
+    const int s = j % TS_S;
+    const int p0 = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT;
+    unsigned char* st = stage0 + s * Sh::SB;
+    mbar_expect_tx(&full[s], Sh::SB);
+    tma_load_3d(st, &md, 0, p0, q, &full[s]);
+    if (NOISE == CSX_NOISE_PERPIXEL) tma_load_2d(st + Sh::DB, &mn, 0, p0, &full[s]);
+  };
+  if (tid == 0)
+    for (int j = 0; j < TS_S && j < my; ++j) issue(j);
   const int* ld = a.labels;
   const int* lt = a.labels + a.npix;
   const int* ls = a.labels + 2 * a.npix;
-  float nb[NB];
-#pragma unroll
-  for (int f = 0; f < NB; ++f) nb[f] = a.ninv_band[f];
-  double acc = 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += gridDim.x * blockDim.x) {
-    const int kd = __ldg(ld + p), kt = __ldg(lt + p), ks = __ldg(ls + p);
-    if ((unsigned)kd >= (unsigned)a.Kd || (unsigned)kt >= (unsigned)a.KT ||
-        (unsigned)ks >= (unsigned)a.Ks) {
-      acc += (double)nan_f();
-      continue;
+  int nkd = 0, nkt = 0, nks = 0;
+  float nw = 1.f;
+  auto fetch = [&](int j) {
+    const int p = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT + tid;
+    if (j < my && p < a.npix) {
+      nkd = __ldg(ld + p);
+      nkt = __ldg(lt + p);
+      nks = __ldg(ls + p);
+      if (NOISE == CSX_NOISE_SEPARABLE) nw = __ldg(a.w + p);
     }
+  };
+  fetch(0);
+  float n0 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) n0 += a.ninv_band[f];
+  float acc = 0.f;
+  bool bad = false;
+  int j = 0;
+  bool timed_out = false;
+  for (; j < my; ++j) {
+    const int s = j % TS_S;
+    const bool ok = mbar_wait_bounded(&full[s], (unsigned)(j / TS_S) & 1u, TS_WAIT_CYCLES);
+    const float4* row = reinterpret_cast<const float4*>(stage0 + s * Sh::SB);
     float dq[NB], du[NB], nn[NB];
-    load_pixel(dq0 + (long long)p * 2 * NB, dq, du);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 v = row[swz128(tid, k)];
+      const float4 u = row[swz128(tid, 4 + k)];
+      dq[4 * k] = v.x; dq[4 * k + 1] = v.y; dq[4 * k + 2] = v.z; dq[4 * k + 3] = v.w;
+      du[4 * k] = u.x; du[4 * k + 1] = u.y; du[4 * k + 2] = u.z; du[4 * k + 3] = u.w;
+    }
     if (NOISE == CSX_NOISE_PERPIXEL) {
-      const float4* n4 = reinterpret_cast<const float4*>(a.ninv_pix + (long long)p * NB);
+      const float4* nr = reinterpret_cast<const float4*>(stage0 + s * Sh::SB + Sh::DB);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float4 v = __ldg(n4 + k);
+        const float4 v = nr[swz64(tid, k)];
         nn[4 * k] = v.x; nn[4 * k + 1] = v.y; nn[4 * k + 2] = v.z; nn[4 * k + 3] = v.w;
       }
-    } else if (NOISE == CSX_NOISE_SEPARABLE) {
-      const float wp = __ldg(a.w + p);
-#pragma unroll
-      for (int f = 0; f < NB; ++f) nn[f] = wp * nb[f];
-    } else {
-#pragma unroll
-      for (int f = 0; f < NB; ++f) nn[f] = nb[f];
     }
-    PixOut o;
-    const bool ok = pixel_eval<GRAD, false>(dq, du, nn, tab + (long long)kd * NB,
-                                            tab + (long long)(a.Kd + kt) * NB,
-                                            tab + (long long)(a.Kd + a.KT + kt) * NB,
-                                            tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.bands, o);
-    if (!ok) {
-      acc += (double)nan_f();
-      continue;
+    int kd = nkd, kt = nkt, ks = nks;
+    const float wp = nw;
+    fetch(j + 1);
+    const int p = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT + tid;
+    bool valid = p < a.npix;
+    if (valid && ((unsigned)kd >= (unsigned)a.Kd || (unsigned)kt >= (unsigned)a.KT ||
+                  (unsigned)ks >= (unsigned)a.Ks)) {
+      bad = true;
+      valid = false;
     }
-    acc += (double)(o.chi2 - o.dnd);
+    // runs of equal labels within the warp: a valid pixel starts one at lane 0, after an invalid
+    // pixel or where a label changes
+    bool head = false;
+    unsigned hb = 0u;
+    if (Sh::RUNS) {
+      const int pkd = __shfl_up_sync(0xffffffffu, kd, 1), pkt = __shfl_up_sync(0xffffffffu, kt, 1),
+                pks = __shfl_up_sync(0xffffffffu, ks, 1);
+      const bool pv = __shfl_up_sync(0xffffffffu, valid, 1);
+      head = valid && (lane == 0 || !pv || kd != pkd || kt != pkt || ks != pks);
+      hb = __ballot_sync(0xffffffffu, head);
+      if (lane == 0) s_cnt[j & 1][warp] = __popc(hb);
+    }
+    if (__syncthreads_or(!ok)) {  // every thread holds its pixel: the stage may be refilled
+      timed_out = true;
+      break;
+    }
+    if (tid == 0 && j + TS_S < my) issue(j + TS_S);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (Sh::RUNS) {
+      int roff = 0, nruns = 0;
+#pragma unroll
+      for (int w = 0; w < TS_NW; ++w) {
+        const int c = s_cnt[j & 1][w];
+        roff += (w < warp) ? c : 0;
+        nruns += c;
+      }
+      const int rid = roff + __popc(hb & ((2u << lane) - 1u)) - 1;  // this pixel's run
+      if (head) s_trip[rid] = make_int4(kd, kt, ks, 0);
+      __syncthreads();
+      for (int r = tid; r < nruns; r += TS_NT) {
+        const int4 t = s_trip[r];
+        run_scalars<GRAD>(tab + (long long)t.x * NB, tab + (long long)(a.Kd + t.y) * NB,
+                          tab + (long long)(a.Kd + a.KT + t.y) * NB,
+                          tab + (long long)(a.Kd + 2 * a.KT + t.z) * NB, a.ninv_band, a.bands,
+                          n0, s_sc + 16 * r);
+      }
+      __syncthreads();
+      if (valid) {
+        float sc[NSC];
+        load_scalars(s_sc + 16 * rid, sc);
+        acc += cell_pixel<GRAD>(dq, du, tab + (long long)kd * NB, tab + (long long)(a.Kd + kt) * NB,
+                                tab + (long long)(a.Kd + a.KT + kt) * NB,
+                                tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.ninv_band, a.bands,
+                                sc, NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f, g0, g1, g2);
+      }
+    } else if (valid) {
+      PixOut o;
+      if (pixel_eval<GRAD, false>(dq, du, nn, tab + (long long)kd * NB,
+                                  tab + (long long)(a.Kd + kt) * NB,
+                                  tab + (long long)(a.Kd + a.KT + kt) * NB,
+                                  tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.bands, o)) {
+        acc += o.chi2 - o.dnd;
+        if (GRAD) {
+          g0 = o.gbd;
+          g1 = o.gtd;
+          g2 = o.gbs;
+        }
+      } else {
+        bad = true;
+      }
+    }
     if (GRAD) {
-      atomicAdd(gacc + kd, o.gbd);
-      atomicAdd(gacc + a.Kd + kt, o.gtd);
-      atomicAdd(gacc + a.Kd + a.KT + ks, o.gbs);
+      if (!valid) kd = kt = ks = -1;
+      warp_run_add3(gacc, kd, g0, gacc + a.Kd, kt, g1, gacc + a.Kd + a.KT, ks, g2);
     }
   }
-  const double tot = block_sum<256>(acc, sred);
-  if (threadIdx.x == 0) atomicAdd(a.L + q, tot);
+  if (timed_out) {
+    if (tid == 0) {
+      for (int jj = j; jj < my && jj < j + TS_S; ++jj)
+        (void)mbar_wait_bounded(&full[jj % TS_S], (unsigned)(jj / TS_S) & 1u, TS_WAIT_CYCLES);
+      atomicAdd(a.L + q, (double)nan_f());
+    }
+    return;
+  }
+  const double tot = block_sum<TS_NT>(bad ? (double)nan_f() : (double)acc, sred);
+  if (tid == 0) atomicAdd(a.L + q, tot);
   if (GRAD && SMEM_GRAD) {
     __syncthreads();
-    for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
+    for (int i = tid; i < a.P; i += TS_NT) {
       const float v = sgrad[i];
       if (v != 0.f) atomicAdd(ggl + i, v);
     }
   }
 }
 
-template <int NOISE, bool GRAD>
-static int spectral_dispatch_smem(const SpecArgs& a, dim3 grid, cudaStream_t s) {
-  const size_t smem = (size_t)a.P * sizeof(float);
-  if (GRAD && smem <= 48 * 1024) {
-    k_spectral<NOISE, GRAD, true><<<grid, 256, smem, s>>>(a);
-  } else {
-    k_spectral<NOISE, GRAD, false><<<grid, 256, 0, s>>>(a);
-  }
+template <int NOISE, bool GRAD, bool SMEM_GRAD>
+static int launch_tma_one(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, dim3 grid,
+                          cudaStream_t s) {
+  const size_t smem = TsShape<NOISE>::smem(a.P, GRAD && SMEM_GRAD);
+  // the attribute covers the ring plus a P-vector of up to 16384 floats
+  CSX_CUDA(cudaFuncSetAttribute(k_spectral_tma<NOISE, GRAD, SMEM_GRAD>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TsShape<NOISE>::smem(16384, true)));
+  k_spectral_tma<NOISE, GRAD, SMEM_GRAD><<<grid, TS_NT, smem, s>>>(md, mn, a);
   CSX_CUDA(cudaGetLastError());
   return CSX_OK;
 }
 
-template <bool GRAD>
-static int spectral_dispatch(const SpecArgs& a, dim3 grid, cudaStream_t s) {
-  switch (a.noise_kind) {
-    case CSX_NOISE_HOMOGENEOUS: return spectral_dispatch_smem<CSX_NOISE_HOMOGENEOUS, GRAD>(a, grid, s);
-    case CSX_NOISE_SEPARABLE: return spectral_dispatch_smem<CSX_NOISE_SEPARABLE, GRAD>(a, grid, s);
-    default: return spectral_dispatch_smem<CSX_NOISE_PERPIXEL, GRAD>(a, grid, s);
+template <int NOISE>
+static int launch_tma(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, bool grad,
+                      dim3 grid, cudaStream_t s) {
+  if (!grad) return launch_tma_one<NOISE, false, false>(md, mn, a, grid, s);
+  if (a.P <= 16384) return launch_tma_one<NOISE, true, true>(md, mn, a, grid, s);
+  return launch_tma_one<NOISE, true, false>(md, mn, a, grid, s);
+}
+
+// Tensor maps of one launch: d as [problems][npix][32 floats] (box 32 x 256 x 1, 128-byte
+// swizzle) and, for per-pixel noise, N^-1 as [npix][16 floats] (box 16 x 256, 64-byte swizzle).
+// Returns false if the encoder is unavailable or refuses (the entry points have already checked
+// that d and N^-1 are 16-byte aligned).
+static bool make_maps(const SpecArgs& a, CUtensorMap* md, CUtensorMap* mn) {
+  if ((reinterpret_cast<uintptr_t>(a.d) & 15) != 0) return false;
+  {
+    const cuuint64_t dims[3] = {2 * NB, (cuuint64_t)a.npix, (cuuint64_t)a.nprob};
+    const cuuint64_t str[2] = {2 * NB * sizeof(float), (cuuint64_t)a.npix * 2 * NB * sizeof(float)};
+    const cuuint32_t box[3] = {2 * NB, TS_NT, 1};
+    if (encode_tiled(md, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.d, dims, str, box,
+                     CU_TENSOR_MAP_SWIZZLE_128B))
+      return false;
   }
+  if (a.noise_kind == CSX_NOISE_PERPIXEL) {
+    if ((reinterpret_cast<uintptr_t>(a.ninv_pix) & 15) != 0) return false;
+    const cuuint64_t dims[2] = {NB, (cuuint64_t)a.npix};
+    const cuuint64_t str[1] = {NB * sizeof(float)};
+    const cuuint32_t box[2] = {NB, TS_NT};
+    if (encode_tiled(mn, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.ninv_pix, dims, str, box,
+                     CU_TENSOR_MAP_SWIZZLE_64B))
+      return false;
+  } else {
+    *mn = *md;  // unused
+  }
+  return true;
+}
+
+// Tiles per CTA of the TMA kernel: up to 8, fewer when that would leave under 4 CTAs per SM slot.
+static int tma_grid_x(int npix, int nprob) {
+  const long long ntile = (npix + TS_NT - 1) / TS_NT;
+  long long tpc = ntile * nprob / (148LL * 2 * 4);
+  tpc = tpc < 1 ? 1 : (tpc > 8 ? 8 : tpc);
+  return (int)((ntile + tpc - 1) / tpc);
 }
 
 int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s) {
-  if (a.nprob == 0) return CSX_OK;
-  // about 8 pixels per thread, at most 65535 problems per launch (grid.y limit)
-  int bx = (a.npix + 256 * 8 - 1) / (256 * 8);
-  if (bx < 1) bx = 1;
+  if (a.nprob == 0 || a.npix == 0) return CSX_OK;
+  // at most 65535 problems per launch (grid.y limit)
   for (int q0 = 0; q0 < a.nprob; q0 += 65535) {
     SpecArgs b = a;
     const int nq = (a.nprob - q0 < 65535) ? a.nprob - q0 : 65535;
@@ -182,8 +351,18 @@ int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s) {
     b.beta = a.beta + (long long)q0 * a.P;
     b.L = a.L + q0;
     b.grad = a.grad ? a.grad + (long long)q0 * a.P : nullptr;
-    dim3 grid(bx, nq);
-    const int rc = grad ? spectral_dispatch<true>(b, grid, s) : spectral_dispatch<false>(b, grid, s);
+    CUtensorMap md, mn;
+    int rc;
+    if (make_maps(b, &md, &mn)) {
+      const dim3 grid(tma_grid_x(b.npix, nq), nq);
+      switch (b.noise_kind) {
+        case CSX_NOISE_HOMOGENEOUS: rc = launch_tma<CSX_NOISE_HOMOGENEOUS>(md, mn, b, grad, grid, s); break;
+        case CSX_NOISE_SEPARABLE: rc = launch_tma<CSX_NOISE_SEPARABLE>(md, mn, b, grad, grid, s); break;
+        default: rc = launch_tma<CSX_NOISE_PERPIXEL>(md, mn, b, grad, grid, s); break;
+      }
+    } else {
+      return fail(CSX_ECUDA, "tensor-map encoding failed (cuTensorMapEncodeTiled)");
+    }
     if (rc) return rc;
   }
   return CSX_OK;

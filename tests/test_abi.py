@@ -1,6 +1,7 @@
 """The C ABI library (no GPU needed): it loads, exports every symbol include/csx.h declares, and
 the binding's ctypes structures have the C layout."""
 import ctypes
+import numpy as np
 import os
 import re
 import subprocess
@@ -69,3 +70,35 @@ def test_host_only_calls(lib):
     # argument errors are reported before touching a device
     rc = lib.csx_mixing(None, 1, None, None, None, None)
     assert rc == -1 and b"model" in lib.csx_last_error()
+
+
+def test_misaligned_pointers_are_rejected_on_the_host(lib):
+    """Pixel rows are read as 16-byte vectors and staged by tensor copies: a data pointer that is
+    not 16-byte aligned (or an int / float / double array off its natural alignment) is refused with
+    CSX_EINVAL before anything touches a device. The pointers below are never dereferenced."""
+    import ctypes
+    from paper_2604_08463_b300 import csx
+    model = csx.Model(np.array([40.0, 100.0, 402.0]))
+    sky = csx.CSky()
+    sky.npix, sky.nreal, sky.noise_kind = 10, 1, 0
+    for f in range(3):
+        sky.ninv_band[f] = 1.0
+    K = (ctypes.c_int32 * 3)(1, 1, 1)
+    ok16, off4 = 0x10000, 0x10004
+    sky.d = off4
+    rc = lib.csx_spectral_like(ctypes.byref(model.c), ctypes.byref(sky), ctypes.c_void_p(ok16), K, 1,
+                               ctypes.c_void_p(ok16), ctypes.c_void_p(ok16), None)
+    assert rc == -1 and b"sky->d must be 16-byte aligned" in lib.csx_last_error()
+    sky.d = ok16
+    rc = lib.csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky), ctypes.c_void_p(ok16 + 2),
+                               K, 1, ctypes.c_void_p(ok16), ctypes.c_void_p(ok16),
+                               ctypes.c_void_p(ok16), None)
+    assert rc == -1 and b"labels must be 4-byte aligned" in lib.csx_last_error()
+    rc = lib.csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky), ctypes.c_void_p(ok16), K,
+                               1, ctypes.c_void_p(ok16), ctypes.c_void_p(off4), ctypes.c_void_p(ok16),
+                               None)
+    assert rc == -1 and b"L must be 8-byte aligned" in lib.csx_last_error()
+    rc = lib.csx_spectral_grad_noalloc(ctypes.byref(model.c), ctypes.byref(sky), ctypes.c_void_p(ok16),
+                                       K, 1, ctypes.c_void_p(ok16 + 1), ctypes.c_void_p(ok16),
+                                       ctypes.c_void_p(ok16), None)
+    assert rc == -1 and b"beta must be 4-byte aligned" in lib.csx_last_error()

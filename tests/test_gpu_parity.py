@@ -99,6 +99,58 @@ def test_spectral_like_and_grad(noise, nside, K):
         assert_grad_close(g[r], gr, Sr)
 
 
+@pytest.mark.parametrize("noise", ["homogeneous", "separable", "perpixel"])
+def test_spectral_kmeans_patches(noise):
+    """K-means patches, as in the workloads: the 32 pixels of a warp of the streaming kernel fall
+    into one to several cells (equal label triples). With separable / homogeneous noise the
+    Gram-Schmidt scalars are formed once per distinct cell of the warp, two cells per round; a warp
+    with one cell, and warps needing two and more rounds, must all match the oracle."""
+    csx = _csx()
+    K = (12, 3, 6)
+    case = Case(workloads.fullsky(16, K, nreal=2), noise)
+    lab = case.wl.labels[0]
+    groups = lab[:, : lab.shape[1] // 32 * 32].reshape(3, -1, 32)
+    ncells = [len(set(zip(*groups[:, w, :]))) for w in range(groups.shape[1])]
+    assert min(ncells) == 1 and max(ncells) >= 5, np.bincount(ncells)
+    model, sky, labels = case.gpu()
+    beta = workloads.random_points(np.array(K), 2, seed=11).astype(np.float32)
+    bt = torch.tensor(beta, device="cuda")
+    L1 = csx.spectral_like(model, sky, labels[0], K, bt)
+    L2, g = csx.spectral_grad(model, sky, labels[0], K, bt)
+    torch.cuda.synchronize()
+    L1, L2, g = L1.cpu().numpy(), L2.cpu().numpy(), g.cpu().numpy()
+    for r in range(2):
+        Lr, gr, Sr = grad_ref(case, r, lab, K, beta[r].astype(np.float64))
+        assert abs(L1[r] - Lr) <= 1e-5 * abs(Lr), (L1[r], Lr)
+        assert abs(L2[r] - Lr) <= 1e-5 * abs(Lr)
+        assert_grad_close(g[r], gr, Sr)
+
+
+def test_spectral_misaligned_data_is_refused():
+    """Data not 16-byte aligned cannot be read as 16-byte pixel vectors nor staged by tensor copies:
+    the call is refused on the host with CSX_EINVAL, nothing is launched, and the same data from an
+    aligned buffer evaluates normally afterwards."""
+    csx = _csx()
+    K = (12, 3, 6)
+    case = Case(workloads.fullsky(16, K, nreal=2), "separable")
+    model, sky, labels = case.gpu()
+    n = case.d32.size
+    raw = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    raw[1:] = torch.from_numpy(case.d32.reshape(-1)).to("cuda")
+    d_off = raw[1:].view(case.d32.shape)
+    assert d_off.data_ptr() % 16 != 0
+    sky_off = csx.Sky(d_off, noise="separable", ninv_band=case.nb32, w=sky.w)
+    beta = torch.tensor(workloads.random_points(np.array(K), 2, seed=12), dtype=torch.float32,
+                        device="cuda")
+    with pytest.raises(csx.CsxError, match="16-byte aligned"):
+        csx.spectral_grad(model, sky_off, labels[0], K, beta)
+    La, ga = csx.spectral_grad(model, sky, labels[0], K, beta)
+    torch.cuda.synchronize()
+    Lr, gr, Sr = grad_ref(case, 0, case.wl.labels[0], K, beta[0].cpu().numpy().astype(np.float64))
+    assert abs(La[0].item() - Lr) <= 1e-5 * abs(Lr)
+    assert_grad_close(ga[0].cpu().numpy(), gr, Sr)
+
+
 def test_spectral_ragged_tails_and_one_pixel_patches():
     csx = _csx()
     # 300 pixels (not a multiple of the block size), every pixel its own beta_d patch
