@@ -8,7 +8,8 @@
 //             moments, kept as residual moments about a reference point (see build_moments and
 //             eval_moment): one pass over the pixels per reference point, then each evaluation
 //             costs O(cells), not O(pixels). The reference point is moved to the current point
-//             (at most 3 times) when the fit converges far from it.
+//             (at most 6 times) when the fit nears convergence far from it or a line search
+//             fails there.
 //     STREAM: per pixel, residual form (any diagonal noise).
 //   the optimiser: L-BFGS (memory m) in variables scaled by the square root of the Gauss-Newton
 //     diagonal at the start point; box bounds handled as in App. A: parameters at a bound whose
@@ -442,34 +443,19 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     atomicAdd(c.gacc + c.Kd + kt, -2.f * gtd);
     atomicAdd(c.gacc + c.Kd + c.KT + ks, -2.f * gbs);
     if (WANT_H) {
-      // projected Gauss-Newton diagonal 2 (sum w s_k^2) (da^T N da - u^T M^-1 u), u = A^T N da,
-      // with sum w s s^T taken at the reference point (Q)
-      float n2[3] = {0.f, 0.f, 0.f}, u0[3] = {0.f, 0.f, 0.f}, u1[3] = {0.f, 0.f, 0.f},
-            u2[3] = {0.f, 0.f, 0.f};
+      // Gauss-Newton diagonal 2 (sum w s_k^2) da^T N da (the scaling of the optimiser's variables;
+      // the same quantity as the streaming path's), with sum w s s^T at the reference point (Q)
+      float n2[3] = {0.f, 0.f, 0.f};
 #pragma unroll 3
       for (int f = 0; f < 15; ++f) {
         const float a1 = pd[f] * bt[f], a2 = ss[f];
         const float da[3] = {a1 * a.bands.lnd[f], a1 * dt[f], a2 * a.bands.lns[f]};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float nda = nb[f] * da[k];
-          n2[k] = fmaf(nda, da[k], n2[k]);
-          u0[k] += nda;
-          u1[k] = fmaf(nda, a1, u1[k]);
-          u2[k] = fmaf(nda, a2, u2[k]);
-        }
+        for (int k = 0; k < 3; ++k) n2[k] = fmaf(nb[f] * da[k], da[k], n2[k]);
       }
       float h[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float uu[3] = {u0[k], u1[k], u2[k]};
-        float quad = 0.f;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) quad = fmaf(uu[i] * v[i][j], uu[j], quad);
-        h[k] = 2.f * (k < 2 ? Q[1][1] : Q[2][2]) * fmaxf(n2[k] - quad, 0.f);
-      }
+      for (int k = 0; k < 3; ++k) h[k] = 2.f * (k < 2 ? Q[1][1] : Q[2][2]) * n2[k];
       atomicAdd(c.hacc + kd, h[0]);
       atomicAdd(c.hacc + c.Kd + kt, h[1]);
       atomicAdd(c.hacc + c.Kd + c.KT + ks, h[2]);
@@ -735,7 +721,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
           ++nev;
           for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
           ++recentres;
-          last_step = 1e30f;
+          --it;  // a move of the reference point is not a quasi-Newton iteration
           __syncthreads();
           continue;
         }
@@ -827,7 +813,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
           ++nev;
           for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
           ++recentres;
-          last_step = 1e30f;
+          --it;
           __syncthreads();
           continue;
         }
