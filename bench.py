@@ -237,6 +237,8 @@ def run_csx(args):
         res = csx.fit_batch(model, sky, labels, K, beta0, **opts)
         rec = csx.reconstruct(model, sky, labels, K, res["beta"], d_fg=fg, metrics=True)
         vt, best = csx.select(rec["metrics"], nconf, nreal)
+        if dist:  # the path's one exchange: V_tot of every rank's configurations, global argmin
+            csx.gather_select(vt)
         return res, rec, vt, best
 
     # the clock sampler starts before the warm-up: starting nvidia-smi stalls CUDA launches briefly
@@ -274,6 +276,8 @@ def run_csx(args):
         host_s["reconstruct"] += time.perf_counter() - t
         t = time.perf_counter()
         vt, best = csx.select(rec["metrics"], nconf, nreal)
+        if dist:
+            csx.gather_select(vt)
         host_s["select"] += time.perf_counter() - t
         rec_ev[k][1].record(stream)
         evals.append(res["nevals"])
@@ -326,6 +330,8 @@ def run_csx(args):
     other_fit = {"path": other, "fit_ms": c0.elapsed_time(c1),
                  "converged": int((res_o["status"].cpu().numpy() == 0).sum()),
                  "iters_mean": float(res_o["iters"].cpu().numpy().mean())}
+
+    streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
 
     # end to end: pinned host inputs -> device, step, results -> host
     e2e = None
@@ -427,6 +433,7 @@ def run_csx(args):
                       "line_search": int((status == 3).sum()), "nonphysical": int((status == 2).sum()),
                       "iters_mean": float(iters.mean()), "evals_mean": float(nev.mean())},
         "other_path_fit": other_fit,
+        "streaming_kernel": streaming,
         "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
@@ -437,6 +444,57 @@ def run_csx(args):
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+STREAM = dict(nside=64, K=(100, 20, 30), nreal=100)
+
+
+def streaming_rates(csx, hbm, ncall=20):
+    """The streaming likelihood (+ adjoint gradient) kernel on its own: one call evaluates L (and
+    dL/dbeta) of 100 problems (the realizations) of the full-sky nside-64 configuration with
+    K = (100, 20, 30) and hit-count (separable) noise, 49152 pixels each: 629 MB of data, more
+    than L2, so every call streams it from HBM. Timed with CUDA events over `ncall` back-to-back
+    calls; a call is the SED-table kernel, two memsets and the streaming kernel."""
+    import numpy as np
+    import torch
+    from synth import workloads
+    wl = workloads.fullsky(STREAM["nside"], STREAM["K"], nreal=STREAM["nreal"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = torch.from_numpy(wl.data()).to(dev)
+    nb = np.zeros(16, np.float32)
+    nb[:wl.sky.nfreq] = wl.sky.ninv_band
+    w = torch.from_numpy(wl.sky.w.astype(np.float32)).to(dev)
+    lab = torch.from_numpy(np.ascontiguousarray(wl.labels[0], dtype=np.int32)).to(dev)
+    K = wl.K[0]
+    beta = torch.from_numpy(np.tile(wl.beta0(0), (wl.nreal, 1)).astype(np.float32)).to(dev)
+    model = csx.Model(wl.sky.nu)
+    sky = csx.Sky(d, noise="separable", ninv_band=nb, w=w)
+    stream = torch.cuda.current_stream()
+    units = wl.nreal * wl.npix
+    out = {"workload": "fullsky_nside%d K=%s R=%d separable noise" % (STREAM["nside"], list(K),
+                                                                     wl.nreal),
+           "pixels_per_call": units, "bytes_per_pixel": BYTES_PER_PIXEL_EVAL,
+           "timing": "CUDA events around %d calls (tables kernel + memsets + streaming kernel)"
+                     % ncall}
+    for name, fn in (("L_and_grad", csx.spectral_grad), ("L", csx.spectral_like)):
+        for _ in range(3):
+            fn(model, sky, lab, K, beta)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ncall):
+            fn(model, sky, lab, K, beta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / ncall
+        gbs = units * BYTES_PER_PIXEL_EVAL / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_call": ms, "cluster_pixel_evals_per_s": units / (ms * 1e-3),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                  "frac": gbs / hbm}}
+    del d, sky
+    torch.cuda.empty_cache()
+    return out
 
 
 def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fits_per_s):
@@ -518,6 +576,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stream", action="store_true", help="skip the streaming-kernel rates")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

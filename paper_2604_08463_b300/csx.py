@@ -301,6 +301,37 @@ def select(metrics: torch.Tensor, nconf: int, nreal: int):
     return v, b
 
 
+def chunk(n: int, world: int, rank: int):
+    """Contiguous share [lo, hi) of n independent problems (or configurations) for `rank` of
+    `world` processes: [floor(k n / W), floor((k + 1) n / W)) (Sec. 3.1)."""
+    if world < 1 or not 0 <= rank < world or n < 0:
+        raise ValueError("need n >= 0 and 0 <= rank < world")
+    return (rank * n) // world, ((rank + 1) * n) // world
+
+
+def gather_select(vtot: torch.Tensor, group=None):
+    """Selection across processes: every rank holds V_tot of its own configurations (in rank
+    order of the global numbering); all ranks receive (V_tot of all configurations, global index
+    of the smallest, ties to the lowest index). The only exchange of the path: one all-gather of
+    per-configuration scalars (nccl for device tensors, gloo for host tensors)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    n = torch.tensor([vtot.numel()], dtype=torch.int64, device=vtot.device)
+    sizes = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(sizes, n, group=group)
+    sizes = [int(x.item()) for x in sizes]
+    m = max(sizes)
+    pad = torch.full((m,), float("inf"), dtype=torch.float64, device=vtot.device)
+    pad[: vtot.numel()] = vtot.to(torch.float64)
+    parts = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad, group=group)
+    allv = torch.cat([p[:k] for p, k in zip(parts, sizes)])
+    # argmin with ties to the lowest index (NaN never wins)
+    key = torch.where(torch.isnan(allv), torch.full_like(allv, float("inf")), allv)
+    best = int(torch.nonzero(key == key.min())[0].item()) if allv.numel() else -1
+    return allv, best
+
+
 class SpectralLikelihood(torch.autograd.Function):
     """L(beta) for one configuration as a differentiable torch op (Sec. 3.3.1).
 

@@ -117,7 +117,20 @@ def many_patch_labels(vec: np.ndarray, ks, key: str = "", processes: int | None 
         work = vec.shape[0] * sum(todo)  # assignment cost ~ pixels x clusters per iteration
         if nproc > 1 and len(todo) > 4 and work > 5e7:
             import multiprocessing as mp
-            with mp.get_context("spawn").Pool(nproc) as pool:
+            # one BLAS thread per worker process (the workers read this when they import numpy)
+            saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                    "MKL_NUM_THREADS")}
+            for v in saved:
+                os.environ[v] = "1"
+            try:
+                pool = mp.get_context("spawn").Pool(nproc)
+            finally:
+                for v, old in saved.items():
+                    if old is None:
+                        os.environ.pop(v, None)
+                    else:
+                        os.environ[v] = old
+            with pool:
                 for k, lab in pool.imap_unordered(_worker, [(vec, k) for k in todo]):
                     _CACHE[(key, vec.shape[0], k)] = lab
                     _to_disk(key, n, k, lab)
