@@ -36,6 +36,11 @@ BYTES_PER_PIXEL_EVAL = 120 + 12 + 4   # 15 bands x Q,U float32 + 3 int32 labels 
 BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12  # residual moments (R, C, Q) + cell labels
 FLOPS_PER_CELL_EVAL = 4600   # FP32 operations of one cell's chi2 + gradient (FMA = 2)
 FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (FMA = 2)
+# DRAM bytes (read + write) per unit from the committed ncu captures (profiles/): the persistent
+# fit per cell evaluation (1000-problem scan, 46.6 M cell evaluations, scaled by units), the
+# streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
+TRAFFIC_FIT_PER_CELL_EVAL = 1053.0
+TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.2, "L": 129.1}
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -388,6 +393,8 @@ def run_csx(args):
             dist.destroy_process_group()
         return
     launches_per_step = 4 + (1 if path == "moment" else 0)
+    # DRAM traffic of one fit launch from the ncu capture (moment path only), scaled by units
+    traffic = TRAFFIC_FIT_PER_CELL_EVAL * unit_evals if path == "moment" else None
     frac_mem, frac_alu = achieved / hbm, achieved_tf / fp32_peak
     if frac_alu >= frac_mem:
         roof = {"kernel": "k_fit (persistent fit)", "bound": "alu", "achieved": achieved_tf,
@@ -395,17 +402,21 @@ def run_csx(args):
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x median SM clock %.0f MHz"
                                % (clocks["sm_mhz"] or 2032.0),
                 "flops_per_unit": FLOPS_PER_CELL_EVAL if path == "moment" else FLOPS_PER_PIXEL_EVAL,
-                "units": unit_evals, "traffic": None,
+                "units": unit_evals, "traffic": traffic,
                 "memory_side": {"achieved_gbs": achieved, "peak_gbs": hbm, "frac": frac_mem}}
     else:
         roof = {"kernel": "k_fit (persistent fit)", "bound": "hbm", "achieved": achieved,
                 "peak": hbm, "unit": "GB/s", "frac": frac_mem,
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "bytes_per_unit": BYTES_PER_CELL_EVAL if path == "moment" else BYTES_PER_PIXEL_EVAL,
-                "units": unit_evals, "traffic": None,
+                "units": unit_evals, "traffic": traffic,
                 "alu_side": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
                              "frac": frac_alu}}
     roof["unit_kind"] = "cell evaluations" if path == "moment" else "pixel evaluations"
+    roof["traffic_source"] = ("profiles/k_fit_moment_scan_nside64.md (ncu, 1000-problem case, "
+                              "scaled by cell evaluations)" if traffic else None)
+    roof["limiter"] = ("latency: per-thread cell evaluations wait on moment loads "
+                       "(ncu long-scoreboard stalls; DRAM 8%, issue 35% active)")
     line = {
         "metric": METRIC,
         "value": world * nprob / (ms_max * 1e-3),
@@ -471,8 +482,8 @@ def streaming_rates(csx, hbm, ncall=20):
     sky = csx.Sky(d, noise="separable", ninv_band=nb, w=w)
     stream = torch.cuda.current_stream()
     units = wl.nreal * wl.npix
-    out = {"workload": "fullsky_nside%d K=%s R=%d separable noise" % (STREAM["nside"], list(K),
-                                                                     wl.nreal),
+    out = {"workload": "fullsky_nside%d K=%s R=%d separable noise"
+                       % (STREAM["nside"], [int(k) for k in K], wl.nreal),
            "pixels_per_call": units, "bytes_per_pixel": BYTES_PER_PIXEL_EVAL,
            "timing": "CUDA events around %d calls (tables kernel + memsets + streaming kernel)"
                      % ncall}
@@ -491,7 +502,9 @@ def streaming_rates(csx, hbm, ncall=20):
         gbs = units * BYTES_PER_PIXEL_EVAL / (ms * 1e-3) / 1e9
         out[name] = {"ms_per_call": ms, "cluster_pixel_evals_per_s": units / (ms * 1e-3),
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                  "frac": gbs / hbm}}
+                                  "frac": gbs / hbm,
+                                  "traffic": TRAFFIC_STREAM_PER_PIXEL[name] * units,
+                                  "traffic_source": "profiles/k_spectral_tma_fullsky_nside64.md"}}
     del d, sky
     torch.cuda.empty_cache()
     return out

@@ -26,7 +26,7 @@ from oracle import reconstruct as rc  # noqa: E402
 from synth import workloads  # noqa: E402
 from tests._inputs import Case, pack, scan_case, small_case  # noqa: E402
 
-TOL_BETA = np.array([1e-3, 1e-2, 1e-3])
+from tests._parity import TOL_BETA, assert_grad_close, grad_ref  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,22 +41,6 @@ def _cuda():
 def _csx():
     from paper_2604_08463_b300 import csx
     return csx
-
-
-def assert_grad_close(g, r, S):
-    g = np.asarray(g, np.float64)
-    r = np.asarray(r, np.float64)
-    scale = np.abs(r).max()
-    assert np.abs(g - r).max() <= 1e-4 * scale, (np.abs(g - r).max() / scale)
-    bad = np.abs(g - r) > 1e-4 * np.abs(r) + 1e-5 * S
-    assert not bad.any(), (np.nonzero(bad)[0][:10], g[bad][:5], r[bad][:5], S[bad][:5])
-
-
-def grad_ref(case, r, lab, K, beta, d64=None, ninv=None):
-    d64 = case.d64(r) if d64 is None else d64
-    ninv = case.ninv64 if ninv is None else ninv
-    L, g = lk.spectral_gradient(case.nu, d64, ninv, lab, K, beta)
-    return L, g, lk.gradient_term_scale(case.nu, d64, ninv, lab, K, beta)
 
 
 # ------------------------------------------------------------------------------ mixing --------
@@ -102,9 +86,9 @@ def test_spectral_like_and_grad(noise, nside, K):
 @pytest.mark.parametrize("noise", ["homogeneous", "separable", "perpixel"])
 def test_spectral_kmeans_patches(noise):
     """K-means patches, as in the workloads: the 32 pixels of a warp of the streaming kernel fall
-    into one to several cells (equal label triples). With separable / homogeneous noise the
-    Gram-Schmidt scalars are formed once per distinct cell of the warp, two cells per round; a warp
-    with one cell, and warps needing two and more rounds, must all match the oracle."""
+    into one to several runs of equal label triples. With separable / homogeneous noise the
+    Gram-Schmidt scalars are formed once per run; warps with one run and with many must all match
+    the oracle."""
     csx = _csx()
     K = (12, 3, 6)
     case = Case(workloads.fullsky(16, K, nreal=2), noise)
