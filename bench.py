@@ -40,7 +40,7 @@ FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (F
 # fit per cell evaluation (1000-problem scan, 46.6 M cell evaluations, scaled by units), the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
 TRAFFIC_FIT_PER_CELL_EVAL = 1053.0
-TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.2, "L": 129.1}
+TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.5, "L": 129.5}
 
 
 def fp32_peak_tflops(sm_mhz):

@@ -90,16 +90,27 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 // L with NaN. Waits are bounded (about 2 s): on time-out the CTA waits (bounded) for its copies
 // still in flight, poisons L with NaN and returns.
 // ---------------------------------------------------------------------------------------------
-constexpr int TS_NT = 256;                          // threads = pixels per tile
+// Build-time tuning switches (the defaults are the measured best on B300): pixels (= threads) per
+// tile, pipeline stages, and the minimum resident CTAs per SM asked of ptxas.
+#ifndef CSX_TS_NT
+#define CSX_TS_NT 128
+#endif
+#ifndef CSX_TS_S
+#define CSX_TS_S 2
+#endif
+#ifndef CSX_TS_MINB
+#define CSX_TS_MINB (512 / CSX_TS_NT)
+#endif
+constexpr int TS_NT = CSX_TS_NT;                    // threads = pixels per tile
 constexpr int TS_NW = TS_NT / 32;
-constexpr int TS_S = 2;                             // pipeline stages
+constexpr int TS_S = CSX_TS_S;                      // pipeline stages
 constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
 
 template <int NOISE>
 struct TsShape {
   static constexpr bool RUNS = NOISE != CSX_NOISE_PERPIXEL;
-  static constexpr int DB = TS_NT * 128;                                 // d: [256][2][16] floats
-  static constexpr int NBY = RUNS ? 0 : TS_NT * 64;                      // N^-1: [256][16] floats
+  static constexpr int DB = TS_NT * 128;                                 // d: [TS_NT][2][16] floats
+  static constexpr int NBY = RUNS ? 0 : TS_NT * 64;                      // N^-1: [TS_NT][16] floats
   static constexpr int SB = DB + NBY;                                    // bytes per stage
   static constexpr int RB = RUNS ? TS_NT * (16 * 4 + 16) : 0;            // run scalars + labels
   static constexpr size_t smem(int P, bool smem_grad) {
@@ -108,7 +119,7 @@ struct TsShape {
 };
 
 template <int NOISE, bool GRAD, bool SMEM_GRAD>
-__global__ void __launch_bounds__(TS_NT, 2)
+__global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
     k_spectral_tma(const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap mn,
                    const SpecArgs a) {
   using Sh = TsShape<NOISE>;
@@ -331,11 +342,13 @@ static bool make_maps(const SpecArgs& a, CUtensorMap* md, CUtensorMap* mn) {
   return true;
 }
 
-// Tiles per CTA of the TMA kernel: up to 8, fewer when that would leave under 4 CTAs per SM slot.
+// Tiles per CTA of the TMA kernel: up to 2048 pixels' worth, fewer when that would leave under
+// 4 CTAs per resident CTA slot.
 static int tma_grid_x(int npix, int nprob) {
   const long long ntile = (npix + TS_NT - 1) / TS_NT;
-  long long tpc = ntile * nprob / (148LL * 2 * 4);
-  tpc = tpc < 1 ? 1 : (tpc > 8 ? 8 : tpc);
+  long long tpc = ntile * nprob / (148LL * CSX_TS_MINB * 4);
+  const long long tmax = 2048 / TS_NT;
+  tpc = tpc < 1 ? 1 : (tpc > tmax ? tmax : tpc);
   return (int)((ntile + tpc - 1) / tpc);
 }
 
