@@ -59,6 +59,11 @@ extern "C" {
 #define CSX_FIT_NONPHYSICAL 2   /* non-finite likelihood at the start (e.g. singular A^T N^-1 A) */
 #define CSX_FIT_LINESEARCH 3    /* no acceptable step from the current point */
 
+/* optimiser of csx_fit_batch: L-BFGS in Gauss-Newton-scaled variables, or AdaTopK (App. A:
+ * AdaBelief directions, Top-K release of bound constraints, dynamic rescaling, backtracking) */
+#define CSX_SOLVER_LBFGS 0
+#define CSX_SOLVER_ADATOPK 1
+
 /* likelihood evaluation inside the fit (AUTO: MOMENT for homogeneous or separable noise with the
  * adjoint gradient, STREAM otherwise) */
 #define CSX_PATH_AUTO 0
@@ -115,6 +120,10 @@ typedef struct csx_fit_opts {
   float xtol[3];        /* 1e-4, 1e-3 K, 1e-4: stop once the quasi-Newton step and the last step of
                            every free parameter are below these (physical units) */
   float fd_step;        /* 1e-3: central-difference step in Gauss-Newton-scaled units (FD mode) */
+  int32_t solver;       /* CSX_SOLVER_LBFGS; CSX_SOLVER_ADATOPK (App. A) needs CSX_GRAD_ADJOINT and
+                           stops once the last two steps of every parameter are below 0.003 xtol */
+  float topk;           /* 0: AdaTopK's Top-K fraction of releasable bound constraints freed per
+                           iteration (0 = the single highest score, 1 = all) */
 } csx_fit_opts;
 
 /* Library version string. */

@@ -104,6 +104,29 @@ def spectral_gradient(nu, d, ninv, labels, K, beta):
     return L, grad
 
 
+def gauss_newton_diagonal(nu, d, ninv, labels, K, beta):
+    """H_theta = 2 sum over the pixels of theta's patch and the Stokes parameters of
+    s_hat_j^2 (dA_j/dtheta)^T N^-1 (dA_j/dtheta), j the column theta enters (the Gauss-Newton
+    diagonal of chi2 without the projection onto the complement of A): a curvature scale per
+    parameter, |dL/dtheta| / H_theta estimating the distance to the optimum along theta."""
+    kd, kt, ks = (int(k) for k in K)
+    bd, td, bs = pixel_parameters(beta, labels, K)
+    A = mixing_matrix(nu, bd, td, bs)
+    dbd, dtd, dbs = mixing_derivatives(nu, bd, td, bs)
+    M, b = normal_equations(A, ninv, d)
+    s = np.linalg.solve(M[:, None, :, :], b[..., None])[..., 0]
+    s1 = (s[:, :, 1] ** 2).sum(axis=1)
+    s2 = (s[:, :, 2] ** 2).sum(axis=1)
+    h_bd = 2.0 * s1 * np.einsum("pf,pf,pf->p", ninv, dbd, dbd)
+    h_td = 2.0 * s1 * np.einsum("pf,pf,pf->p", ninv, dtd, dtd)
+    h_bs = 2.0 * s2 * np.einsum("pf,pf,pf->p", ninv, dbs, dbs)
+    return np.concatenate([
+        np.bincount(labels[0], weights=h_bd, minlength=kd),
+        np.bincount(labels[1], weights=h_td, minlength=kt),
+        np.bincount(labels[2], weights=h_bs, minlength=ks),
+    ])
+
+
 def gradient_term_scale(nu, d, ninv, labels, K, beta, data_scale=False):
     """S_theta = 2 sum over the pixels of theta's patch, the Stokes parameters and the bands of
     |w_r (dA/dtheta) s_hat| : the summed magnitude of the terms whose signed sum is dL/dtheta.

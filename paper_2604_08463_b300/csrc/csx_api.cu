@@ -238,6 +238,8 @@ int csx_fit_defaults(csx_fit_opts* o) {
     o->xtol[j] = xt[j];
   }
   o->fd_step = 1e-3f;
+  o->solver = CSX_SOLVER_LBFGS;
+  o->topk = 0.f;
   return CSX_OK;
 }
 
@@ -372,6 +374,11 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   }
   if (o.lower[1] <= 0.f) return fail(CSX_EINVAL, "T_d lower bound must be > 0");
   if (o.grad_mode == CSX_GRAD_FD && !(o.fd_step > 0)) return fail(CSX_EINVAL, "fd_step must be > 0");
+  if (o.solver != CSX_SOLVER_LBFGS && o.solver != CSX_SOLVER_ADATOPK)
+    return fail(CSX_EINVAL, "unknown solver");
+  if (o.solver == CSX_SOLVER_ADATOPK && o.grad_mode != CSX_GRAD_ADJOINT)
+    return fail(CSX_EINVAL, "AdaTopK needs the adjoint gradient");
+  if (!(o.topk >= 0.f && o.topk <= 1.f)) return fail(CSX_EINVAL, "topk must be in [0, 1]");
   int path = o.path;
   if (path == CSX_PATH_AUTO)
     path = (sky->noise_kind != CSX_NOISE_PERPIXEL && o.grad_mode == CSX_GRAD_ADJOINT) ? CSX_PATH_MOMENT
@@ -456,7 +463,7 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   long long slot_floats = 0;
   fit_slot_floats(Pmax, rows_max, ncell_max, o.history, path, &slot_floats);
   int grid = 0;
-  if ((rc = fit_grid(o.threads, path, o.grad_mode, &grid))) return rc;
+  if ((rc = fit_grid(o.threads, path, o.grad_mode, o.solver, &grid))) return rc;
   if ((long long)grid > nprob) grid = (int)nprob;
   float* slots = (float*)scratch(SCR_FIT_SLOTS, (size_t)grid * slot_floats * sizeof(float), &rc);
   if (rc) return rc;
@@ -501,6 +508,8 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
     a.xtol[j] = o.xtol[j];
   }
   a.fd_step = o.fd_step;
+  a.solver = o.solver;
+  a.topk = o.topk;
   TraceSpan tr("fit: kernel", s);
   return launch_fit(a, o.threads, grid, s);
 }

@@ -94,11 +94,13 @@ struct FitArgs {
   int history, max_iter, max_ls;
   int path, grad_mode;
   float lower[3], upper[3], xtol[3], fd_step;
+  int solver;
+  float topk;
 };
 int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s);
 int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path,
                     long long* out);
-int fit_grid(int threads, int path, int grad_mode, int* grid);
+int fit_grid(int threads, int path, int grad_mode, int solver, int* grid);
 
 struct ReconArgs {
   Bands bands;

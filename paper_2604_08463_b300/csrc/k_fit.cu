@@ -865,7 +865,311 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
   __syncthreads();
 }
 
-template <int NT, int PATH, int GMODE, int NOISE>
+// ------------------------------------------------------------------------- AdaTopK --------------
+// App. A: internal space y = (x - l) / (u - l); pivots p in {-1, 0, 1} (lower bound, free, upper
+// bound); per iteration: release the bound constraints whose score p_i g_i is positive (Top-K:
+// max(1, floor(topk n)) of the n candidates, highest first, ties to the lowest index; the printed
+// score has the opposite sign of its stated intent, the alignment of -g with the way into the box,
+// which is followed here), project the gradient onto the free set, rescale the objective and the
+// AdaBelief moments by 1 / |g_proj| when |g_proj| leaves [1e-15, 1e15], AdaBelief direction
+// (beta1 0.9, beta2 0.999, eps 1e-16, bias-corrected) masked to the free set, step limit at the
+// nearest bound, backtracking line search from min(eta, alpha_max) (Armijo 1e-4; accepted also when
+// the value change is below 1e-5 |f| and the slope at the trial point is still downhill, as the FP32
+// likelihood -- residual moments included -- cannot resolve smaller changes), clamp and pin the limiting parameter when the step
+// reaches the bound. A non-descent direction or a failed search resets the AdaBelief state and
+// retries with the normalised projected steepest descent. The direction is zeroed where a free
+// parameter sits on a bound and points out of the box. Stop: no positive release score, the last
+// two steps of every parameter below 0.003 xtol, and every free parameter's Newton-step estimate
+// |dL/dx_i| / H_ii below xtol_i (H: the Gauss-Newton diagonal, evaluated at the candidate point);
+// a candidate that fails the last test restarts the AdaBelief moments. eta: 0.1 at the start, min(1, 2 alpha) after
+// an accepted step of nonzero length. Moment path: the reference point moves to the current point when the fit is
+// 1000 xtol away from it or converging more than 0.09 xtol away (at most 24 times). Slot vectors: z = y, g = scaled internal gradient, p = direction, zt/gt = trial,
+// hs = pivots, first rows of S/Y = AdaBelief m/s.
+constexpr float ADA_B1 = 0.9f, ADA_B2 = 0.999f, ADA_EPS = 1e-16f;
+constexpr float ADA_STEP_FACTOR = 0.003f;
+constexpr int ADA_MAX_RECENTRES = 24;
+constexpr double ADA_EPS_REL = 1e-5;  // value changes below this fraction of |f| are unresolved
+
+template <int NT, int PATH, int NOISE>
+__device__ void fit_problem_adatopk(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int q,
+                                    long long poff) {
+  const int P = c.P;
+  const int tid = threadIdx.x;
+  float* y = c.z;
+  float* g = c.g;
+  float* dv = c.p;
+  float* yt = c.zt;
+  float* gt = c.gt;
+  float* piv = c.hs;
+  float* mm = c.S;
+  float* ssq = c.Y;
+  auto rng = [&](int i) { const int t = ptype(c, i); return a.upper[t] - a.lower[t]; };
+  auto low = [&](int i) { return a.lower[ptype(c, i)]; };
+  auto thr = [&](int i) { return ADA_STEP_FACTOR * a.xtol[ptype(c, i)] / rng(i); };
+  for (int i = tid; i < P; i += NT) {
+    const int t = ptype(c, i);
+    const float x0 = fminf(fmaxf(a.beta0[poff + i], a.lower[t]), a.upper[t]);
+    const float yi = fminf(fmaxf((x0 - a.lower[t]) / (a.upper[t] - a.lower[t]), 0.f), 1.f);
+    y[i] = yi;
+    piv[i] = yi <= 0.f ? -1.f : (yi >= 1.f ? 1.f : 0.f);
+    mm[i] = 0.f;
+    ssq[i] = 0.f;
+    c.x[i] = x0;
+  }
+  __syncthreads();
+  double dnd = 0.0;
+  int recentres = 0;
+  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem);
+  double f = objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, false>(a, c, sh, dnd);
+  int nev = 1, status = CSX_FIT_MAXITER, it = 0;
+  if (!isfinite(f)) {
+    for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.x[i];
+    if (tid == 0) {
+      a.L_out[q] = (double)nan_f();
+      a.status[q] = CSX_FIT_NONPHYSICAL;
+      a.iters[q] = 0;
+      if (a.nevals) a.nevals[q] = nev;
+    }
+    __syncthreads();
+    return;
+  }
+  double scale = 1.0;
+  for (int i = tid; i < P; i += NT) g[i] = c.gacc[i] * rng(i);
+  __syncthreads();
+  float eta = 0.1f;
+  int tb = 0, small = 0;
+  float b1t = 1.f, b2t = 1.f;  // beta1^t, beta2^t
+  for (it = 0; it < a.max_iter; ++it) {
+    // ---- release (Top-K) ----------------------------------------------------------------
+    int ncand = 0;
+    for (int i = tid; i < P; i += NT) ncand += (piv[i] != 0.f && piv[i] * g[i] > 0.f) ? 1 : 0;
+    ncand = block_sum<NT>(ncand, reinterpret_cast<int*>(sh.red));
+    const int nrel = ncand > 0 ? max(1, (int)floorf(a.topk * (float)ncand)) : 0;
+    for (int r = 0; r < nrel; ++r) {
+      float bv = -INFINITY;
+      int bi = 0x7fffffff;
+      for (int i = tid; i < P; i += NT) {
+        const float sc = piv[i] * g[i];
+        if (piv[i] != 0.f && sc > 0.f && sc > bv) {
+          bv = sc;
+          bi = i;
+        }
+      }
+      const float best = block_max<NT>(bv, reinterpret_cast<float*>(sh.red));
+      int mine = (bv == best && best > -INFINITY) ? bi : 0x7fffffff;
+      mine = block_min<NT>(mine, reinterpret_cast<int*>(sh.red));
+      if (tid == 0 && mine < P) piv[mine] = 0.f;
+      __syncthreads();
+    }
+    // ---- project, rescale -----------------------------------------------------------------
+    double gn2 = 0.0;
+    for (int i = tid; i < P; i += NT) {
+      const float gi = (piv[i] == 0.f) ? g[i] : 0.f;
+      gn2 += (double)gi * (double)gi;
+    }
+    gn2 = block_sum<NT>(gn2, sh.red);
+    const double gn = sqrt(gn2);
+    if (gn > 0.0 && (gn < 1e-15 || gn > 1e15)) {
+      const double fs = 1.0 / gn;
+      scale *= fs;
+      f *= fs;
+      for (int i = tid; i < P; i += NT) {
+        g[i] = (float)(g[i] * fs);
+        mm[i] = (float)(mm[i] * fs);
+        ssq[i] = (float)(ssq[i] * fs * fs);
+      }
+      __syncthreads();
+    }
+    if (nrel == 0 && gn == 0.0) {
+      status = CSX_FIT_CONVERGED;
+      break;
+    }
+    // ---- AdaBelief direction --------------------------------------------------------------
+    ++tb;
+    b1t *= ADA_B1;
+    b2t *= ADA_B2;
+    double slope = 0.0;
+    for (int i = tid; i < P; i += NT) {
+      const bool fr = piv[i] == 0.f;
+      const float gi = fr ? g[i] : 0.f;
+      const float m = ADA_B1 * mm[i] + (1.f - ADA_B1) * gi;
+      const float dg = gi - m;
+      const float s2 = ADA_B2 * ssq[i] + (1.f - ADA_B2) * dg * dg + ADA_EPS;
+      mm[i] = m;
+      ssq[i] = s2;
+      float di = fr ? -(m / (1.f - b1t)) / (sqrtf(s2 / (1.f - b2t)) + ADA_EPS) : 0.f;
+      if ((y[i] <= 0.f && di < 0.f) || (y[i] >= 1.f && di > 0.f)) di = 0.f;  // out of the box
+      dv[i] = di;
+      slope += (double)gi * (double)di;
+    }
+    slope = block_sum<NT>(slope, sh.red);
+    const double eps_f = ADA_EPS_REL * fabs(f);
+    bool accepted = false;
+    float alpha = 0.f, amax = 0.f;
+    int jlim = 0x7fffffff;
+    double ft = 0.0, dnd_t = 0.0;
+    for (int attempt = 0; attempt < 2 && !accepted; ++attempt) {
+      if (attempt == 1 || !(slope < 0.0)) {
+        // reset the AdaBelief state; normalised projected steepest descent
+        tb = 0;
+        b1t = b2t = 1.f;
+        float gmax = 0.f;
+        for (int i = tid; i < P; i += NT) {
+          mm[i] = 0.f;
+          ssq[i] = 0.f;
+          if (piv[i] == 0.f) gmax = fmaxf(gmax, fabsf(g[i]));
+        }
+        gmax = block_max<NT>(gmax, reinterpret_cast<float*>(sh.red));
+        if (!(gmax > 0.f)) break;
+        slope = 0.0;
+        for (int i = tid; i < P; i += NT) {
+          const float gi = (piv[i] == 0.f) ? g[i] : 0.f;
+          float di = -gi / gmax;
+          if ((y[i] <= 0.f && di < 0.f) || (y[i] >= 1.f && di > 0.f)) di = 0.f;
+          dv[i] = di;
+          slope += (double)gi * (double)di;
+        }
+        slope = block_sum<NT>(slope, sh.red);
+      }
+      // step limit: nearest bound along d (lowest index on ties)
+      float lv = INFINITY;
+      int li = 0x7fffffff;
+      for (int i = tid; i < P; i += NT) {
+        const float di = dv[i];
+        const float lim = di < 0.f ? -y[i] / di : (di > 0.f ? (1.f - y[i]) / di : INFINITY);
+        if (lim < lv) {
+          lv = lim;
+          li = i;
+        }
+      }
+      amax = block_min<NT>(lv, reinterpret_cast<float*>(sh.red));
+      int mine = (lv == amax) ? li : 0x7fffffff;
+      jlim = block_min<NT>(mine, reinterpret_cast<int*>(sh.red));
+      alpha = fminf(eta, amax);
+      for (int ls = 0; ls < a.max_ls; ++ls) {
+        for (int i = tid; i < P; i += NT) {
+          float v = fminf(fmaxf(y[i] + alpha * dv[i], 0.f), 1.f);
+          if (alpha == amax && i == jlim) v = dv[i] < 0.f ? 0.f : 1.f;
+          yt[i] = v;
+          c.x[i] = low(i) + rng(i) * v;
+        }
+        __syncthreads();
+        ft = objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, false>(a, c, sh, dnd_t) * scale;
+        ++nev;
+        double st = 0.0;
+        for (int i = tid; i < P; i += NT) {
+          const float gi = (float)(c.gacc[i] * rng(i) * scale);
+          gt[i] = gi;
+          st += (double)gi * (double)dv[i];
+        }
+        st = block_sum<NT>(st, sh.red);
+        if (isfinite(ft) && isfinite(st) &&
+            ((ft <= f + 1e-4 * alpha * slope) || (ft <= f + eps_f && st <= 0.0))) {
+          accepted = true;
+          break;
+        }
+        alpha *= 0.5f;
+      }
+    }
+    if (!accepted) {
+      if (PATH == CSX_PATH_MOMENT && recentres < ADA_MAX_RECENTRES) {
+        // the moment form rounds in proportion to the distance from the reference point
+        float dref = 0.f;
+        for (int i = tid; i < P; i += NT)
+          dref = fmaxf(dref, fabsf(low(i) + rng(i) * y[i] - c.xr[i]) / (ADA_STEP_FACTOR * a.xtol[ptype(c, i)]));
+        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+        if (dref > 1.f) {
+          for (int i = tid; i < P; i += NT) c.x[i] = low(i) + rng(i) * y[i];
+          __syncthreads();
+          dnd = recentre<NT, NOISE>(a, c, sh, smem);
+          f = objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, false>(a, c, sh, dnd) * scale;
+          ++nev;
+          for (int i = tid; i < P; i += NT) g[i] = (float)(c.gacc[i] * rng(i) * scale);
+          ++recentres;
+          --it;
+          __syncthreads();
+          continue;
+        }
+      }
+      status = CSX_FIT_LINESEARCH;
+      break;
+    }
+    // ---- accept ----------------------------------------------------------------------------
+    float stepr = 0.f, newt = 0.f;
+    int pos = 0;
+    for (int i = tid; i < P; i += NT) {
+      stepr = fmaxf(stepr, fabsf(yt[i] - y[i]) / thr(i));
+      y[i] = yt[i];
+      g[i] = gt[i];
+      if (alpha == amax && i == jlim) piv[i] = dv[i] < 0.f ? -1.f : 1.f;
+    }
+    __syncthreads();
+    for (int i = tid; i < P; i += NT) pos += (piv[i] != 0.f && piv[i] * g[i] > 0.f) ? 1 : 0;
+    stepr = block_max<NT>(stepr, reinterpret_cast<float*>(sh.red));
+    pos = block_sum<NT>(pos, reinterpret_cast<int*>(sh.red));
+    f = ft;
+    if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
+    if (alpha > 0.f) eta = fminf(1.f, 2.f * alpha);
+    small = (stepr <= 1.f) ? small + 1 : 0;
+    if (PATH == CSX_PATH_MOMENT && recentres < ADA_MAX_RECENTRES) {
+      // move the reference point here when the fit has gone far from it (the moment form rounds in
+      // proportion to that distance; first-order steps are short, so the path is long) or, near
+      // convergence, unless it is already close
+      float dref = 0.f;
+      for (int i = tid; i < P; i += NT)
+        dref = fmaxf(dref, fabsf(low(i) + rng(i) * y[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
+      dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+      if (dref > 1000.f || (small >= 2 && dref > 30.f * ADA_STEP_FACTOR)) {
+        for (int i = tid; i < P; i += NT) c.x[i] = low(i) + rng(i) * y[i];
+        __syncthreads();
+        dnd = recentre<NT, NOISE>(a, c, sh, smem);
+        f = objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, false>(a, c, sh, dnd) * scale;
+        ++nev;
+        for (int i = tid; i < P; i += NT) g[i] = (float)(c.gacc[i] * rng(i) * scale);
+        ++recentres;
+        small = 0;
+        __syncthreads();
+        continue;
+      }
+    }
+    if (small >= 2 && pos == 0) {
+      // candidate stop: the Gauss-Newton diagonal at this point (one more evaluation, same
+      // gradient) gives each free parameter's Newton-step estimate |dL/dx_i| / H_ii
+      for (int i = tid; i < P; i += NT) c.x[i] = low(i) + rng(i) * y[i];
+      __syncthreads();
+      double dn2 = dnd;
+      (void)objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, true>(a, c, sh, dn2);
+      ++nev;
+      for (int i = tid; i < P; i += NT)
+        if (piv[i] == 0.f && c.hacc[i] > 0.f)
+          newt = fmaxf(newt, fabsf(c.gacc[i]) / (c.hacc[i] * a.xtol[ptype(c, i)]));
+      newt = block_max<NT>(newt, reinterpret_cast<float*>(sh.red));
+      if (newt <= 1.f) {
+        status = CSX_FIT_CONVERGED;
+        break;
+      }
+      // still far along some parameter while the steps are short: restart the AdaBelief moments
+      small = 0;
+      tb = 0;
+      b1t = b2t = 1.f;
+      for (int i = tid; i < P; i += NT) {
+        mm[i] = 0.f;
+        ssq[i] = 0.f;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = low(i) + rng(i) * y[i];
+  if (tid == 0) {
+    a.L_out[q] = f / scale - dnd;  // L = chi2_min - sum d^T N d
+    a.status[q] = status;
+    a.iters[q] = min(it + 1, a.max_iter);
+    if (a.nevals) a.nevals[q] = nev;
+  }
+  __syncthreads();
+}
+
+template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
 __global__ void __launch_bounds__(NT, (PATH == CSX_PATH_MOMENT && NT == 128) ? CSX_FIT_MIN_BLOCKS : 1)
 k_fit(const __grid_constant__ FitArgs a) {
   __shared__ Shared sh;
@@ -912,7 +1216,10 @@ k_fit(const __grid_constant__ FitArgs a) {
     c.mom = c.xr + Pm;
     c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * a.ncell_max);
     c.smem = build_smem;
-    fit_problem<NT, PATH, GMODE, NOISE>(a, c, sh, build_smem, q, pd.poff);
+    if (SOLVER == CSX_SOLVER_ADATOPK)
+      fit_problem_adatopk<NT, PATH, NOISE>(a, c, sh, build_smem, q, pd.poff);
+    else
+      fit_problem<NT, PATH, GMODE, NOISE>(a, c, sh, build_smem, q, pd.poff);
   }
 }
 
@@ -934,34 +1241,34 @@ constexpr size_t fit_dyn_smem() {
   return PATH == CSX_PATH_MOMENT ? (build > rows ? build : rows) * sizeof(float) : 0;
 }
 
-template <int NT, int PATH, int GMODE, int NOISE>
+template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
 static int prepare_kernel() {
   const size_t dyn = fit_dyn_smem<NT, PATH>();
   if (dyn > 0)
-    CSX_CUDA(cudaFuncSetAttribute(k_fit<NT, PATH, GMODE, NOISE>,
+    CSX_CUDA(cudaFuncSetAttribute(k_fit<NT, PATH, GMODE, NOISE, SOLVER>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   return CSX_OK;
 }
 
-template <int NT, int PATH, int GMODE, int NOISE>
+template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
 static int occupancy_grid(int* grid) {
   int dev = 0, sms = 0, per = 0;
-  int rc = prepare_kernel<NT, PATH, GMODE, NOISE>();
+  int rc = prepare_kernel<NT, PATH, GMODE, NOISE, SOLVER>();
   if (rc) return rc;
   CSX_CUDA(cudaGetDevice(&dev));
   CSX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fit<NT, PATH, GMODE, NOISE>, NT,
+  CSX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fit<NT, PATH, GMODE, NOISE, SOLVER>, NT,
                                                          fit_dyn_smem<NT, PATH>()));
   if (per < 1) per = 1;
   *grid = sms * per;
   return CSX_OK;
 }
 
-template <int NT, int PATH, int GMODE, int NOISE>
+template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
 static int launch_one(const FitArgs& a, int grid, cudaStream_t s) {
-  int rc = prepare_kernel<NT, PATH, GMODE, NOISE>();
+  int rc = prepare_kernel<NT, PATH, GMODE, NOISE, SOLVER>();
   if (rc) return rc;
-  k_fit<NT, PATH, GMODE, NOISE><<<grid, NT, fit_dyn_smem<NT, PATH>(), s>>>(a);
+  k_fit<NT, PATH, GMODE, NOISE, SOLVER><<<grid, NT, fit_dyn_smem<NT, PATH>(), s>>>(a);
   CSX_CUDA(cudaGetLastError());
   return CSX_OK;
 }
@@ -973,34 +1280,48 @@ static int fit_threads(int threads, int path) {
   return threads == 256 ? 256 : 128;
 }
 
-int fit_grid(int threads, int path, int grad_mode, int* grid) {
+int fit_grid(int threads, int path, int grad_mode, int solver, int* grid) {
   constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT, FD = CSX_GRAD_FD;
-  constexpr int SE = CSX_NOISE_SEPARABLE;
-  if (path == M)
-    return fit_threads(threads, path) == 128 ? occupancy_grid<128, M, AD, SE>(grid)
-                                             : occupancy_grid<256, M, AD, SE>(grid);
-  if (grad_mode == FD) return occupancy_grid<256, ST, FD, SE>(grid);
-  return occupancy_grid<256, ST, AD, SE>(grid);
+  constexpr int SE = CSX_NOISE_SEPARABLE, LB = CSX_SOLVER_LBFGS, AT = CSX_SOLVER_ADATOPK;
+  const bool ada = solver == AT;
+  if (path == M) {
+    if (fit_threads(threads, path) == 128)
+      return ada ? occupancy_grid<128, M, AD, SE, AT>(grid) : occupancy_grid<128, M, AD, SE, LB>(grid);
+    return ada ? occupancy_grid<256, M, AD, SE, AT>(grid) : occupancy_grid<256, M, AD, SE, LB>(grid);
+  }
+  if (grad_mode == FD) return occupancy_grid<256, ST, FD, SE, LB>(grid);
+  return ada ? occupancy_grid<256, ST, AD, SE, AT>(grid) : occupancy_grid<256, ST, AD, SE, LB>(grid);
+}
+
+template <int SOLVER>
+static int launch_adjoint(const FitArgs& a, int threads, int grid, cudaStream_t s) {
+  constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT;
+  constexpr int HO = CSX_NOISE_HOMOGENEOUS, SE = CSX_NOISE_SEPARABLE, PP = CSX_NOISE_PERPIXEL;
+  if (a.path == M) {
+    const bool sep = a.noise_kind == SE;
+    if (fit_threads(threads, M) == 128)
+      return sep ? launch_one<128, M, AD, SE, SOLVER>(a, grid, s)
+                 : launch_one<128, M, AD, HO, SOLVER>(a, grid, s);
+    return sep ? launch_one<256, M, AD, SE, SOLVER>(a, grid, s)
+               : launch_one<256, M, AD, HO, SOLVER>(a, grid, s);
+  }
+  if (a.noise_kind == SE) return launch_one<256, ST, AD, SE, SOLVER>(a, grid, s);
+  if (a.noise_kind == HO) return launch_one<256, ST, AD, HO, SOLVER>(a, grid, s);
+  return launch_one<256, ST, AD, PP, SOLVER>(a, grid, s);
 }
 
 int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s) {
   if (a.nprob == 0) return CSX_OK;
   CSX_CUDA(cudaMemsetAsync(a.head, 0, sizeof(int), s));
-  constexpr int M = CSX_PATH_MOMENT, ST = CSX_PATH_STREAM, AD = CSX_GRAD_ADJOINT, FD = CSX_GRAD_FD;
+  constexpr int ST = CSX_PATH_STREAM, FD = CSX_GRAD_FD, LB = CSX_SOLVER_LBFGS;
   constexpr int HO = CSX_NOISE_HOMOGENEOUS, SE = CSX_NOISE_SEPARABLE, PP = CSX_NOISE_PERPIXEL;
-  if (a.path == M) {
-    const bool sep = a.noise_kind == SE;
-    if (fit_threads(threads, M) == 128)
-      return sep ? launch_one<128, M, AD, SE>(a, grid, s) : launch_one<128, M, AD, HO>(a, grid, s);
-    return sep ? launch_one<256, M, AD, SE>(a, grid, s) : launch_one<256, M, AD, HO>(a, grid, s);
-  } else if (a.grad_mode == FD) {
-    if (a.noise_kind == SE) return launch_one<256, ST, FD, SE>(a, grid, s);
-    if (a.noise_kind == HO) return launch_one<256, ST, FD, HO>(a, grid, s);
-    return launch_one<256, ST, FD, PP>(a, grid, s);
+  if (a.grad_mode == FD) {
+    if (a.noise_kind == SE) return launch_one<256, ST, FD, SE, LB>(a, grid, s);
+    if (a.noise_kind == HO) return launch_one<256, ST, FD, HO, LB>(a, grid, s);
+    return launch_one<256, ST, FD, PP, LB>(a, grid, s);
   }
-  if (a.noise_kind == SE) return launch_one<256, ST, AD, SE>(a, grid, s);
-  if (a.noise_kind == HO) return launch_one<256, ST, AD, HO>(a, grid, s);
-  return launch_one<256, ST, AD, PP>(a, grid, s);
+  if (a.solver == CSX_SOLVER_ADATOPK) return launch_adjoint<CSX_SOLVER_ADATOPK>(a, threads, grid, s);
+  return launch_adjoint<LB>(a, threads, grid, s);
 }
 
 }  // namespace csx

@@ -18,6 +18,7 @@ NMETRIC = 8
 NOISE = {"homogeneous": 0, "separable": 1, "perpixel": 2}
 PATH = {"auto": 0, "stream": 1, "moment": 2}
 GRAD = {"adjoint": 0, "fd": 1}
+SOLVER = {"lbfgs": 0, "adatopk": 1}
 STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search"}
 M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
@@ -47,7 +48,7 @@ class CFitOpts(ctypes.Structure):
     _fields_ = [("max_iter", c_int32), ("history", c_int32), ("max_ls", c_int32),
                 ("path", c_int32), ("grad_mode", c_int32), ("threads", c_int32),
                 ("lower", c_float * 3), ("upper", c_float * 3), ("xtol", c_float * 3),
-                ("fd_step", c_float)]
+                ("fd_step", c_float), ("solver", c_int32), ("topk", c_float)]
 
 
 _lib = None
@@ -234,6 +235,8 @@ def fit_options(**kw) -> CFitOpts:
             v = PATH[v] if isinstance(v, str) else v
         if k == "grad_mode":
             v = GRAD[v] if isinstance(v, str) else v
+        if k == "solver":
+            v = SOLVER[v] if isinstance(v, str) else v
         if k in ("lower", "upper", "xtol"):
             arr = getattr(o, k)
             for j in range(3):

@@ -311,6 +311,80 @@ def test_fit_small_scan(path):
     print("worst |err|/tol", worst)
 
 
+# ------------------------------------------------------------------------------ AdaTopK -------
+@pytest.mark.parametrize("path", ["moment", "stream"])
+def test_adatopk_fit_plain_nside8(path):
+    """AdaTopK (App. A) reaches the oracle optimum; its value agrees with the AdaTopK oracle's."""
+    from oracle import adatopk as oat
+    csx = _csx()
+    wl = workloads.plain(8)
+    case = Case(wl, "homogeneous")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(wl.beta0(0), dtype=torch.float32, device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0, path=path, solver="adatopk", max_iter=5000)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in res.items()}
+    assert out["status"][0] == 0, out
+    ratio, L_ref = _check_fit(case, out, 0, 0, 0)
+    assert abs(out["L"][0] - L_ref) <= 1e-5 * abs(L_ref)
+    x_at, L_at, info = oat.fit(case.nu, case.d64(0), case.ninv64, wl.labels[0], wl.K[0], wl.beta0(0),
+                               workloads.LOWER, workloads.UPPER)
+    assert info["status"] == 0 and abs(out["L"][0] - L_at) <= 1e-5 * abs(L_at)
+
+
+def test_adatopk_start_on_bounds_is_released():
+    """Every parameter starts on a bound (beta_d at its upper, T_d at its lower, beta_s at its upper
+    bound); the gradient points into the box, the constraints are released one per iteration
+    (K = 0) and the fit reaches the interior optimum."""
+    csx = _csx()
+    wl = workloads.plain(8)
+    case = Case(wl, "homogeneous")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor([workloads.UPPER[0], workloads.LOWER[1], workloads.UPPER[2]],
+                         dtype=torch.float32, device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0, solver="adatopk", max_iter=5000)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in res.items()}
+    assert out["status"][0] == 0, out
+    _check_fit(case, out, 0, 0, 0)
+
+
+@pytest.mark.parametrize("path", ["moment", "stream"])
+def test_adatopk_fit_small_scan(path):
+    csx = _csx()
+    case = scan_case(nside=16, nconf=5, kmax=30, nreal=2)
+    wl = case.wl
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(pack(wl, [wl.beta0(c) for c in range(wl.nconf) for _ in range(wl.nreal)]),
+                         device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0, path=path, solver="adatopk",
+                        max_iter=5000)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in res.items()}
+    offs, _ = csx.param_offsets(wl.K, wl.nreal)
+    worst = 0.0
+    for c in range(wl.nconf):
+        for r in range(wl.nreal):
+            q = c * wl.nreal + r
+            assert out["status"][q] == 0, (q, out["status"][q], out["iters"][q])
+            ratio, L_ref = _check_fit(case, out, c, r, offs[q])
+            worst = max(worst, ratio.max())
+            assert abs(out["L"][q] - L_ref) <= 1e-5 * abs(L_ref)
+    print("worst |err|/tol", worst, "iterations", out["iters"].mean())
+
+
+def test_adatopk_options_are_checked():
+    csx = _csx()
+    wl = workloads.plain(8)
+    case = Case(wl, "homogeneous")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(wl.beta0(0), dtype=torch.float32, device="cuda")
+    with pytest.raises(csx.CsxError, match="adjoint"):
+        csx.fit_batch(model, sky, labels, wl.K, beta0, solver="adatopk", grad_mode="fd")
+    with pytest.raises(csx.CsxError, match="topk"):
+        csx.fit_batch(model, sky, labels, wl.K, beta0, solver="adatopk", topk=1.5)
+
+
 # ------------------------------------------------------------------------ reconstruction ------
 def test_reconstruct_and_select():
     csx = _csx()
