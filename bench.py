@@ -336,6 +336,33 @@ def run_csx(args):
                  "converged": int((res_o["status"].cpu().numpy() == 0).sum()),
                  "iters_mean": float(res_o["iters"].cpu().numpy().mean())}
 
+    # AdaTopK (App. A) on the same problems, untimed comparison with the L-BFGS fit
+    ada = None
+    if rank == 0 and not args.no_adatopk:
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        res_a = csx.fit_batch(model, sky, labels, K, beta0, solver="adatopk", max_iter=5000)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        st_a = res_a["status"].cpu().numpy()
+        offs, _ = csx.param_offsets(K, nreal)
+        ptype = np.concatenate([np.concatenate([np.full(int(k[j]), j) for j in range(3)])
+                                for k in K for _ in range(nreal)])
+        tolv = np.array([1e-3, 1e-2, 1e-3])[ptype]
+        dev_ = np.abs(res_a["beta"].cpu().numpy() - res["beta"].cpu().numpy()) / tolv
+        dL = res_a["L"].cpu().numpy() - res["L"].cpu().numpy()
+        ada = {"fit_ms": a0.elapsed_time(a1), "converged": int((st_a == 0).sum()),
+               "max_iter": int((st_a == 1).sum()), "line_search": int((st_a == 3).sum()),
+               "iters_mean": float(res_a["iters"].cpu().numpy().mean()),
+               "evals_mean": float(res_a["nevals"].cpu().numpy().mean()),
+               "beta_vs_lbfgs_over_tol": {"p50": float(np.median(dev_)),
+                                          "p99": float(np.percentile(dev_, 99)),
+                                          "frac_above_1": float((dev_ > 1).mean())},
+               "L_minus_lbfgs": {"median": float(np.median(dL)), "max": float(dL.max()),
+                                 "frac_lower": float((dL < 0).mean())}}
+
     streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
 
     # end to end: pinned host inputs -> device, step, results -> host
@@ -445,6 +472,7 @@ def run_csx(args):
                       "iters_mean": float(iters.mean()), "evals_mean": float(nev.mean())},
         "other_path_fit": other_fit,
         "streaming_kernel": streaming,
+        "adatopk_fit": ada,
         "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
@@ -590,6 +618,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stream", action="store_true", help="skip the streaming-kernel rates")
+    ap.add_argument("--no-adatopk", action="store_true", help="skip the AdaTopK comparison fit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
