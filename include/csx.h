@@ -241,6 +241,23 @@ int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const
 int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot, int32_t* best,
                void* stream);
 
+/* Seeded spherical K-means patches (Sec. 2.2) for nlab cluster counts at once, on the device: the
+ * Lloyd iterations of the input generator (assignment by the largest dot product formed as
+ * (x cx + y cy) + z cz in float64 without fused multiply-add, first cluster on ties; member sums in
+ * increasing pixel order; an emptied cluster re-seeded at the pixel of smallest best dot product,
+ * the i-th emptied cluster taking the i-th in (value, index) order; renormalisation by
+ * sqrt((x x + y y) + z z); stop when an assignment repeats or after max_iter assignments; labels
+ * renumbered by first appearance), so the labels are bit-exact with that generator.
+ *   vec:    device [n][3] unit vectors (float64, 8-byte aligned)
+ *   K:      host [nlab] cluster counts; K <= 1 gives one patch, K >= n one pixel per patch,
+ *           otherwise 2..2048
+ *   init:   device int32, for each labeling with 1 < K < n (in order) its K distinct starting
+ *           pixels, concatenated (the seeded draw is the caller's)
+ *   labels: device [nlab][n] output; iters: device [nlab] assignments made, or NULL
+ * Errors: CSX_EINVAL for bad sizes, NULL or misaligned pointers. Asynchronous on `stream`. */
+int csx_kmeans(const double* vec, int32_t n, int32_t nlab, const int32_t* K, const int32_t* init,
+               int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

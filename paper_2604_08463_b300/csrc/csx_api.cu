@@ -584,6 +584,45 @@ int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const
   return launch_recon(a, s);
 }
 
+int csx_kmeans(const double* vec, int32_t n, int32_t nlab, const int32_t* K, const int32_t* init,
+               int32_t max_iter, int32_t* labels, int32_t* iters, void* stream) {
+  if (n < 1 || nlab < 0) return fail(CSX_EINVAL, "n must be >= 1 and nlab >= 0");
+  if (nlab == 0) return CSX_OK;
+  if (!vec || !K || !labels) return fail(CSX_EINVAL, "NULL argument");
+  if (max_iter < 1) return fail(CSX_EINVAL, "max_iter must be >= 1");
+  CSX_ALIGN(vec, 8);
+  CSX_ALIGN(init, 4);
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(iters, 4);
+  std::vector<long long> ioff((size_t)nlab);
+  long long total = 0;
+  int kmax = 1;
+  for (int L = 0; L < nlab; ++L) {
+    if (K[L] < 1) return fail(CSX_EINVAL, "every K must be >= 1");
+    ioff[L] = total;
+    if (K[L] > 1 && K[L] < n) {
+      if (K[L] > KMEANS_KMAX)
+        return fail(CSX_EINVAL, "K above " + std::to_string(KMEANS_KMAX) + " (and below n)");
+      total += K[L];
+      kmax = std::max(kmax, (int)K[L]);
+    }
+  }
+  if (total > 0 && !init) return fail(CSX_EINVAL, "init is NULL");
+  int rc = CSX_OK;
+  const size_t best_b = (size_t)nlab * n * sizeof(double);
+  const size_t k_b = ((size_t)nlab * sizeof(int) + 15) & ~size_t(15);
+  char* scr = (char*)scratch(SCR_KMEANS, best_b + k_b + (size_t)nlab * sizeof(long long), &rc);
+  if (rc) return rc;
+  double* best = (double*)scr;
+  int* K_dev = (int*)(scr + best_b);
+  long long* ioff_dev = (long long*)(scr + best_b + k_b);
+  cudaStream_t s = (cudaStream_t)stream;
+  CSX_CUDA(cudaMemcpyAsync(K_dev, K, (size_t)nlab * sizeof(int), cudaMemcpyHostToDevice, s));
+  CSX_CUDA(cudaMemcpyAsync(ioff_dev, ioff.data(), (size_t)nlab * sizeof(long long),
+                           cudaMemcpyHostToDevice, s));
+  return launch_kmeans(vec, n, nlab, K_dev, ioff_dev, init, max_iter, kmax, labels, best, iters, s);
+}
+
 int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot, int32_t* best,
                void* stream) {
   if (nconf < 1 || nreal < 1) return fail(CSX_EINVAL, "nconf and nreal must be >= 1");

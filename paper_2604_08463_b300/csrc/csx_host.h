@@ -29,6 +29,7 @@ enum ScratchId {
   SCR_CELLS,        // cell structure of the fit (perm, offsets, counts)
   SCR_MISC,         // small counters
   SCR_RECON_DESC,
+  SCR_KMEANS,       // K-means: per-labeling best dot products, cluster counts and offsets
   SCR_COUNT
 };
 void* scratch(ScratchId id, size_t bytes, int* err);
@@ -66,6 +67,12 @@ int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s);
 
 int launch_cells(int npix, int nconf, const int* labels, const int* K_dev, int* perm,
                  int* cell_off, int* ncell, cudaStream_t s);
+
+constexpr int KMEANS_KMAX = 2048;
+size_t kmeans_smem(int kmax);
+int launch_kmeans(const double* vec, int n, int nlab, const int* K_dev, const long long* ioff_dev,
+                  const int* init, int max_iter, int kmax, int* labels, double* best, int* iters,
+                  cudaStream_t s);
 
 struct FitArgs {
   Bands bands;

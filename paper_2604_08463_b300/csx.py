@@ -24,7 +24,7 @@ M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
            "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_noalloc",
-           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select"]
+           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select", "csx_kmeans"]
 
 
 class CsxError(RuntimeError):
@@ -77,6 +77,7 @@ def lib():
         L.csx_reconstruct.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32, vp, vp, vp,
                                       vp, vp, vp, vp]
         L.csx_select.argtypes = [i32, i32, vp, vp, vp, vp]
+        L.csx_kmeans.argtypes = [vp, i32, i32, pi32, vp, i32, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("csx_version", "csx_last_error"):
                 getattr(L, name).restype = i32
@@ -302,6 +303,28 @@ def select(metrics: torch.Tensor, nconf: int, nreal: int):
     b = torch.empty(1, dtype=torch.int32, device=metrics.device)
     _check(lib().csx_select(nconf, nreal, _ptr(metrics.contiguous()), _ptr(v), _ptr(b), _stream()))
     return v, b
+
+
+def kmeans(vec: torch.Tensor, K, init, max_iter: int = 30):
+    """Seeded spherical K-means labels (Sec. 2.2) for every cluster count in K at once.
+
+    vec: [n, 3] float64 CUDA unit vectors; K: sequence of cluster counts; init: for each K with
+    1 < K < n, its K distinct starting pixels (the seeded draw is the caller's). Returns
+    (labels [len(K), n] int32, iters [len(K)] int32) as device tensors."""
+    vec = vec.to(torch.float64).contiguous()
+    n = vec.shape[0]
+    Kh, Kp = _host_i32(np.asarray(K).reshape(-1))
+    nvalid = int(((Kh > 1) & (Kh < n)).sum())
+    if len(init) != nvalid:
+        raise ValueError("init needs one array per cluster count with 1 < K < n (%d)" % nvalid)
+    parts = [np.asarray(x, dtype=np.int32) for x in init]
+    flat = np.concatenate(parts) if parts else np.zeros(1, np.int32)
+    init_d = torch.from_numpy(flat).to(vec.device)
+    labels = torch.empty((Kh.size, n), dtype=torch.int32, device=vec.device)
+    iters = torch.empty(Kh.size, dtype=torch.int32, device=vec.device)
+    _check(lib().csx_kmeans(_ptr(vec), n, int(Kh.size), Kp, _ptr(init_d), int(max_iter),
+                            _ptr(labels), _ptr(iters), _stream()))
+    return labels, iters
 
 
 def chunk(n: int, world: int, rank: int):

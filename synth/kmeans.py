@@ -18,14 +18,24 @@ import numpy as np
 _CACHE: dict = {}
 
 
-def _assign(vec, cent, chunk=8192):
+def _assign(vec, cent, chunk=4096):
+    """Label of the largest dot product (first on ties) and its value. The dot product is formed
+    element by element as (x cx + y cy) + z cz, each product and sum rounded once in float64 (no
+    fused multiply-add, no BLAS reordering), so that any implementation doing the same operations
+    in the same order assigns identically."""
     lab = np.empty(vec.shape[0], dtype=np.int64)
     best = np.empty(vec.shape[0])
     for s in range(0, vec.shape[0], chunk):
-        dots = vec[s:s + chunk] @ cent.T
+        v = vec[s:s + chunk]
+        dots = (v[:, 0:1] * cent[:, 0] + v[:, 1:2] * cent[:, 1]) + v[:, 2:3] * cent[:, 2]
         lab[s:s + chunk] = np.argmax(dots, axis=1)
         best[s:s + chunk] = dots[np.arange(dots.shape[0]), lab[s:s + chunk]]
     return lab, best
+
+
+def init_indices(n: int, k: int, seed: int) -> np.ndarray:
+    """The K distinct starting pixels of a labeling (seeded), as spherical_kmeans draws them."""
+    return np.random.default_rng(seed).choice(n, size=k, replace=False)
 
 
 def spherical_kmeans(vec: np.ndarray, k: int, seed: int, max_iter: int = 30) -> np.ndarray:
@@ -35,8 +45,7 @@ def spherical_kmeans(vec: np.ndarray, k: int, seed: int, max_iter: int = 30) -> 
         return np.arange(n, dtype=np.int32)
     if k <= 1:
         return np.zeros(n, dtype=np.int32)
-    rng = np.random.default_rng(seed)
-    cent = vec[rng.choice(n, size=k, replace=False)].copy()
+    cent = vec[init_indices(n, k, seed)].copy()
     labels = None
     for _ in range(max_iter):
         new, best = _assign(vec, cent)
@@ -44,12 +53,13 @@ def spherical_kmeans(vec: np.ndarray, k: int, seed: int, max_iter: int = 30) -> 
             break
         labels = new
         counts = np.bincount(labels, minlength=k)
+        # member sums in increasing pixel order (bincount accumulates sequentially)
         sums = np.stack([np.bincount(labels, weights=vec[:, c], minlength=k) for c in range(3)], 1)
         empty = np.nonzero(counts == 0)[0]
         if empty.size:
             far = np.argsort(best, kind="stable")[:empty.size]
             sums[empty] = vec[far]
-        norm = np.linalg.norm(sums, axis=1)
+        norm = np.sqrt((sums[:, 0] * sums[:, 0] + sums[:, 1] * sums[:, 1]) + sums[:, 2] * sums[:, 2])
         norm[norm == 0] = 1.0
         cent = sums / norm[:, None]
     _, first = np.unique(labels, return_index=True)
@@ -64,7 +74,7 @@ def _disk_path(key: str, n: int, k: int):
     d = os.environ.get("CSX_KMEANS_CACHE")
     if not d or not key:
         return None
-    return os.path.join(d, "km_%s_%d_%d.npy" % (key, n, k))
+    return os.path.join(d, "km2_%s_%d_%d.npy" % (key, n, k))
 
 
 def _from_disk(key, n, k):
