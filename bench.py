@@ -364,6 +364,7 @@ def run_csx(args):
                                  "frac_lower": float((dL < 0).mean())}}
 
     streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
+    kmeans_gpu = kmeans_rates(csx, inp) if (rank == 0 and not args.no_kmeans) else None
 
     # end to end: pinned host inputs -> device, step, results -> host
     e2e = None
@@ -473,6 +474,7 @@ def run_csx(args):
         "other_path_fit": other_fit,
         "streaming_kernel": streaming,
         "adatopk_fit": ada,
+        "kmeans": kmeans_gpu,
         "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
@@ -536,6 +538,42 @@ def streaming_rates(csx, hbm, ncall=20):
     del d, sky
     torch.cuda.empty_cache()
     return out
+
+
+def kmeans_rates(csx, inp):
+    """GPU spherical K-means (the step before the hot path): every distinct patch count of the
+    scan (one labeling each, 32512 cut-sky pixels) in one launch, timed with CUDA events, and
+    checked against the scan's labels from the input generator (bit-exact)."""
+    import numpy as np
+    import torch
+    from synth import healpix, kmeans as km
+    wl = inp["wl"]
+    pix = healpix.galactic_cut(SCAN["nside"], SCAN["b_cut_deg"])
+    vec = healpix.unit_vectors(SCAN["nside"])[pix]
+    n = vec.shape[0]
+    ks = sorted({int(k) for k in wl.K.reshape(-1)})
+    init = [km.init_indices(n, k, 100 + k) for k in ks if 1 < k < n]
+    vd = torch.from_numpy(vec).to(torch.device("cuda", torch.cuda.current_device()))
+    csx.kmeans(vd, ks, init)  # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lab, iters = csx.kmeans(vd, ks, init)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lab = lab.cpu().numpy()
+    # the generator's labeling of each K, from the scan's configurations
+    ref = {}
+    for c in range(wl.nconf):
+        for j in range(3):
+            ref.setdefault(int(wl.K[c, j]), wl.labels[c, j])
+    mismatched = sum(int(not np.array_equal(lab[i], ref[k])) for i, k in enumerate(ks))
+    return {"labelings": len(ks), "pixels": n, "ms": ms, "labelings_per_s": len(ks) / (ms * 1e-3),
+            "iters_mean": float(iters.float().mean()), "mismatched_vs_generator": mismatched,
+            "timing": "CUDA events around one csx_kmeans launch (one CTA per labeling)"}
 
 
 def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fits_per_s):
@@ -619,6 +657,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stream", action="store_true", help="skip the streaming-kernel rates")
     ap.add_argument("--no-adatopk", action="store_true", help="skip the AdaTopK comparison fit")
+    ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU K-means rates")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
