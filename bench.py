@@ -39,7 +39,7 @@ FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (F
 # DRAM bytes (read + write) per unit from the committed ncu captures (profiles/): the persistent
 # fit per cell evaluation (1000-problem scan, 46.6 M cell evaluations, scaled by units), the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
-TRAFFIC_FIT_PER_CELL_EVAL = 1053.0
+TRAFFIC_FIT_PER_CELL_EVAL = 1054.0
 TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.5, "L": 129.5}
 
 

@@ -31,8 +31,12 @@ namespace csx {
 //   CSX_FIT_STAGE_MOMENTS  1: a cell's 171 moments are staged into shared memory by cp.async
 //                          before use; 0: read from global memory (L2) where used.
 //   CSX_FIT_MIN_BLOCKS     minimum resident 128-thread moment-path CTAs per SM asked of ptxas.
+//   CSX_FIT_PREFETCH       1: prefetch each thread's next cell's moments into L2.
 #ifndef CSX_FIT_STAGE_MOMENTS
 #define CSX_FIT_STAGE_MOMENTS 0
+#endif
+#ifndef CSX_FIT_PREFETCH
+#define CSX_FIT_PREFETCH 0
 #endif
 #ifndef CSX_FIT_MIN_BLOCKS
 #define CSX_FIT_MIN_BLOCKS 4
@@ -289,6 +293,19 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     }
 #else
     const float* ms = c.mom + cell;
+#if CSX_FIT_PREFETCH
+    {
+      // bring the thread's next cell's moments towards L2 while this cell is evaluated (the
+      // moments of all resident problems exceed L2; a warp's prefetches cover whole lines)
+      const int nxt = cell + NT;
+      if (nxt < c.ncell) {
+        const float* mn = c.mom + nxt;
+#pragma unroll 9
+        for (int e = 0; e < NM; ++e)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(mn + (long long)e * c.ncell));
+      }
+    }
+#endif
 #endif
     // M = A^T N A and Z = A_r^T N A
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
