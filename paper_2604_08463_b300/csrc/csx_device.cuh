@@ -400,7 +400,8 @@ __device__ __forceinline__ void run_scalars(const float* __restrict__ pd,
                                             const float* __restrict__ bt,
                                             const float* __restrict__ dt,
                                             const float* __restrict__ ss, const float* nband,
-                                            const Bands& bc, float n0, float* out) {
+                                            const Bands& bc, float n0, float* out,
+                                            float* vec = nullptr) {
   float ad[NB], as[NB];
   {
     float p[NB], b[NB];
@@ -450,6 +451,92 @@ __device__ __forceinline__ void run_scalars(const float* __restrict__ pd,
   o[1] = make_float4(mu2, nu, u[0], u[1]);
   o[2] = make_float4(u[2], u[3], u[4], u[5]);
   o[3] = make_float4(u[6], u[7], u[8], 0.f);
+  if (vec) {
+    // the run's band vectors (see cell_pixel): e1 = n c1, e2 = n c2 and, for the gradient,
+    // n A_d ln(nu/nu0_d), n A_d dlnB/dT, n A_s ln(nu/nu0_s); [5][16] floats
+    float d[NB];
+    if (GRAD) load_row16(dt, d);
+#pragma unroll
+    for (int f = 0; f < NB; ++f) {
+      const float n = nband[f];
+      const float e1 = n * (ad[f] - mu1);
+      vec[f] = e1;
+      vec[NB + f] = fmaf(-nu, e1, n * (as[f] - mu2));
+      if (GRAD) {
+        const float nad = n * ad[f];
+        vec[2 * NB + f] = nad * bc.lnd[f];
+        vec[3 * NB + f] = nad * d[f];
+        vec[4 * NB + f] = n * as[f] * bc.lns[f];
+      }
+    }
+  }
+}
+
+// One pixel in its run's basis with the run's band vectors precomputed (run_scalars `vec`):
+// the same quantities as cell_pixel, from 12 dot products over the bands.
+template <bool GRAD>
+__device__ __forceinline__ float cell_pixel_vec(const float (&dq)[NB], const float (&du)[NB],
+                                                const float* nband, const float* vec,
+                                                const float (&sc)[15], float w, float& gbd,
+                                                float& gtd, float& gbs) {
+  float t0q = 0.f, t1q = 0.f, t2q = 0.f, t0u = 0.f, t1u = 0.f, t2u = 0.f;
+  float bq = 0.f, tq = 0.f, sq = 0.f, bu = 0.f, tu = 0.f, su = 0.f;
+  const float4* v4 = reinterpret_cast<const float4*>(vec);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 e1 = v4[k], e2 = v4[4 + k];
+    float4 vb, vt, vs;
+    if (GRAD) {
+      vb = v4[8 + k];
+      vt = v4[12 + k];
+      vs = v4[16 + k];
+    }
+    const float a1[4] = {e1.x, e1.y, e1.z, e1.w}, a2[4] = {e2.x, e2.y, e2.z, e2.w};
+    float b1[4], b2[4], b3[4];
+    if (GRAD) {
+      b1[0] = vb.x; b1[1] = vb.y; b1[2] = vb.z; b1[3] = vb.w;
+      b2[0] = vt.x; b2[1] = vt.y; b2[2] = vt.z; b2[3] = vt.w;
+      b3[0] = vs.x; b3[1] = vs.y; b3[2] = vs.z; b3[3] = vs.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int f = 4 * k + c;
+      const float xq = dq[f], xu = du[f];
+      t0q = fmaf(nband[f], xq, t0q);
+      t0u = fmaf(nband[f], xu, t0u);
+      t1q = fmaf(a1[c], xq, t1q);
+      t1u = fmaf(a1[c], xu, t1u);
+      t2q = fmaf(a2[c], xq, t2q);
+      t2u = fmaf(a2[c], xu, t2u);
+      if (GRAD) {
+        bq = fmaf(b1[c], xq, bq);
+        bu = fmaf(b1[c], xu, bu);
+        tq = fmaf(b2[c], xq, tq);
+        tu = fmaf(b2[c], xu, tu);
+        sq = fmaf(b3[c], xq, sq);
+        su = fmaf(b3[c], xu, su);
+      }
+    }
+  }
+  const float i0 = sc[0], i1 = sc[1], i2 = sc[2], mu1 = sc[3], mu2 = sc[4], nu = sc[5];
+  if (GRAD) {
+    const float s2q = t2q * i2, s2u = t2u * i2;
+    const float s1q = fmaf(-nu, s2q, t1q * i1), s1u = fmaf(-nu, s2u, t1u * i1);
+    const float s0q = t0q * i0 - mu1 * s1q - mu2 * s2q;
+    const float s0u = t0u * i0 - mu1 * s1u - mu2 * s2u;
+    const float rbq = bq - (s0q * sc[6] + s1q * sc[7] + s2q * sc[8]);
+    const float rbu = bu - (s0u * sc[6] + s1u * sc[7] + s2u * sc[8]);
+    const float rtq = tq - (s0q * sc[9] + s1q * sc[10] + s2q * sc[11]);
+    const float rtu = tu - (s0u * sc[9] + s1u * sc[10] + s2u * sc[11]);
+    const float rsq = sq - (s0q * sc[12] + s1q * sc[13] + s2q * sc[14]);
+    const float rsu = su - (s0u * sc[12] + s1u * sc[13] + s2u * sc[14]);
+    const float m2w = -2.f * w;
+    gbd = m2w * fmaf(s1q, rbq, s1u * rbu);
+    gtd = m2w * fmaf(s1q, rtq, s1u * rtu);
+    gbs = m2w * fmaf(s2q, rsq, s2u * rsu);
+  }
+  return -w * (i0 * fmaf(t0q, t0q, t0u * t0u) + i1 * fmaf(t1q, t1q, t1u * t1u) +
+               i2 * fmaf(t2q, t2q, t2u * t2u));
 }
 
 __device__ __forceinline__ void load_scalars(const float* __restrict__ src, float (&sc)[NSC]) {

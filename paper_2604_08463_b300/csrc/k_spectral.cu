@@ -79,9 +79,11 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 // tile ahead; a stage is refilled after the barrier that follows its last read.
 //
 // Separable / homogeneous noise: the pixels of a tile are split into runs of consecutive pixels
-// with equal labels (within a warp); the Gram-Schmidt scalars of each run are formed once, by one
-// thread, into a shared run table (run_scalars), and every pixel is then evaluated in its run's
-// basis (cell_pixel). Per-pixel noise: each pixel's own Gram-Schmidt solve (pixel_eval).
+// with equal labels (within a warp); the Gram-Schmidt scalars of each run -- and, for L alone and
+// the first TS_RUNVEC runs of a tile, its band vectors -- are formed once, by one thread, into a
+// shared run table (run_scalars), and every pixel is then evaluated in its run's basis
+// (cell_pixel_vec from the stored vectors; cell_pixel from the SED table rows otherwise: with the
+// gradient, the stored-vector form measured slower, its three extra vectors costing registers). Per-pixel noise: each pixel's own Gram-Schmidt solve (pixel_eval).
 //
 // L_p is accumulated in FP32 per thread (a few pixels) and in FP64 across the block, then added to
 // L[problem] with one FP64 atomic per block; gradients go to a shared-memory copy of the problem's
@@ -105,6 +107,7 @@ constexpr int TS_NT = CSX_TS_NT;                    // threads = pixels per tile
 constexpr int TS_NW = TS_NT / 32;
 constexpr int TS_S = CSX_TS_S;                      // pipeline stages
 constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
+constexpr int TS_RUNVEC = 32;  // runs per tile whose band vectors are kept in the run table
 
 template <int NOISE>
 struct TsShape {
@@ -112,7 +115,7 @@ struct TsShape {
   static constexpr int DB = TS_NT * 128;                                 // d: [TS_NT][2][16] floats
   static constexpr int NBY = RUNS ? 0 : TS_NT * 64;                      // N^-1: [TS_NT][16] floats
   static constexpr int SB = DB + NBY;                                    // bytes per stage
-  static constexpr int RB = RUNS ? TS_NT * (16 * 4 + 16) : 0;            // run scalars + labels
+  static constexpr int RB = RUNS ? TS_NT * (16 * 4 + 16) + TS_RUNVEC * 80 * 4 : 0;  // run table
   static constexpr size_t smem(int P, bool smem_grad) {
     return 1024 + (size_t)TS_S * SB + RB + (smem_grad ? (size_t)P * sizeof(float) : 0);
   }
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   unsigned char* stage0 = ts_smem + (((off + 1023u) & ~1023u) - off);  // 1024-byte aligned ring
   float* s_sc = reinterpret_cast<float*>(stage0 + TS_S * Sh::SB);      // [TS_NT][16] run scalars
   int4* s_trip = reinterpret_cast<int4*>(s_sc + (Sh::RUNS ? TS_NT * 16 : 0));  // [TS_NT] labels
+  float* s_vec = reinterpret_cast<float*>(s_trip + (Sh::RUNS ? TS_NT : 0));    // [TS_RUNVEC][80]
   float* sgrad = reinterpret_cast<float*>(stage0 + TS_S * Sh::SB + Sh::RB);
   const int q = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ntile = (a.npix + TS_NT - 1) / TS_NT;
@@ -242,16 +246,21 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
         run_scalars<GRAD>(tab + (long long)t.x * NB, tab + (long long)(a.Kd + t.y) * NB,
                           tab + (long long)(a.Kd + a.KT + t.y) * NB,
                           tab + (long long)(a.Kd + 2 * a.KT + t.z) * NB, a.ninv_band, a.bands,
-                          n0, s_sc + 16 * r);
+                          n0, s_sc + 16 * r, (!GRAD && r < TS_RUNVEC) ? s_vec + 80 * r : nullptr);
       }
       __syncthreads();
       if (valid) {
         float sc[NSC];
         load_scalars(s_sc + 16 * rid, sc);
-        acc += cell_pixel<GRAD>(dq, du, tab + (long long)kd * NB, tab + (long long)(a.Kd + kt) * NB,
-                                tab + (long long)(a.Kd + a.KT + kt) * NB,
-                                tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.ninv_band, a.bands,
-                                sc, NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f, g0, g1, g2);
+        const float wpx = NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f;
+        if (!GRAD && rid < TS_RUNVEC)
+          acc += cell_pixel_vec<GRAD>(dq, du, a.ninv_band, s_vec + 80 * rid, sc, wpx, g0, g1, g2);
+        else
+          acc += cell_pixel<GRAD>(dq, du, tab + (long long)kd * NB,
+                                  tab + (long long)(a.Kd + kt) * NB,
+                                  tab + (long long)(a.Kd + a.KT + kt) * NB,
+                                  tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.ninv_band,
+                                  a.bands, sc, wpx, g0, g1, g2);
       }
     } else if (valid) {
       PixOut o;
