@@ -8,8 +8,8 @@
 //             moments, kept as residual moments about a reference point (see build_moments and
 //             eval_moment): one pass over the pixels per reference point, then each evaluation
 //             costs O(cells), not O(pixels). The reference point is moved to the current point
-//             (at most 6 times) when the fit nears convergence far from it or a line search
-//             fails there.
+//             (at most 6 times) when the fit converges far from it or a line search fails
+//             there.
 //     STREAM: per pixel, residual form (any diagonal noise).
 //   the optimiser: L-BFGS (memory m) in variables scaled by the square root of the Gauss-Newton
 //     diagonal at the start point; box bounds handled as in App. A: parameters at a bound whose
@@ -32,8 +32,13 @@ namespace csx {
 //                          before use; 0: read from global memory (L2) where used.
 //   CSX_FIT_MIN_BLOCKS     minimum resident 128-thread moment-path CTAs per SM asked of ptxas.
 //   CSX_FIT_PREFETCH       1: prefetch each thread's next cell's moments into L2.
+//   CSX_FIT_NEAR           step size (in xtol) below which the reference point first moves to
+//                          the current point (0: only at convergence).
 #ifndef CSX_FIT_STAGE_MOMENTS
 #define CSX_FIT_STAGE_MOMENTS 0
+#endif
+#ifndef CSX_FIT_NEAR
+#define CSX_FIT_NEAR 0.f
 #endif
 #ifndef CSX_FIT_PREFETCH
 #define CSX_FIT_PREFETCH 0
@@ -718,14 +723,15 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         break;
       }
     }
-    const bool near_opt = recentres == 0 && stepn <= 100.f && last_step <= 100.f;
+    const bool near_opt = CSX_FIT_NEAR > 0.f && recentres == 0 && stepn <= CSX_FIT_NEAR &&
+                          last_step <= CSX_FIT_NEAR;
     const bool at_opt = recentres < 6 && stepn <= 1.f && last_step <= 1.f;
     if (PATH == CSX_PATH_MOMENT && it > 0 && (near_opt || at_opt)) {
       {
-        // The moment form rounds in proportion to the distance from the reference point: once the
-        // steps are within 100 tolerances of the optimum (first time), and again at convergence,
-        // move the reference here unless it is already close, so that the last iterations run on
-        // precise values. Each move costs one pass over the pixels.
+        // The moment form rounds in proportion to the distance from the reference point: at
+        // convergence (and, with CSX_FIT_NEAR > 0, also once the steps first fall within that many
+        // tolerances), move the reference here unless it is already close, so that the last
+        // iterations run on precise values. Each move costs one pass over the pixels.
         float dref = 0.f;
         for (int i = tid; i < P; i += NT)
           dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
@@ -1187,7 +1193,8 @@ __device__ void fit_problem_adatopk(const FitArgs& a, Ctx& c, Shared& sh, float*
 }
 
 template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
-__global__ void __launch_bounds__(NT, (PATH == CSX_PATH_MOMENT && NT == 128) ? CSX_FIT_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(NT, (PATH == CSX_PATH_MOMENT && NT <= 128)
+                                         ? CSX_FIT_MIN_BLOCKS * (128 / NT) : 1)
 k_fit(const __grid_constant__ FitArgs a) {
   __shared__ Shared sh;
   __shared__ int s_q;
@@ -1290,11 +1297,12 @@ static int launch_one(const FitArgs& a, int grid, cudaStream_t s) {
   return CSX_OK;
 }
 
-// CTA size: the moment path runs 128-thread CTAs by default (two problems per SM overlap their
-// barriers), the streaming path 256; `threads` (128 or 256) overrides it for the moment path.
+// CTA size: the moment path runs 128-thread CTAs by default (four problems per SM overlap their
+// barriers), the streaming path 256; `threads` (64, 128 or 256) overrides it for the moment path
+// (64 with L-BFGS only).
 static int fit_threads(int threads, int path) {
   if (path != CSX_PATH_MOMENT) return 256;
-  return threads == 256 ? 256 : 128;
+  return (threads == 256 || threads == 64) ? threads : 128;
 }
 
 int fit_grid(int threads, int path, int grad_mode, int solver, int* grid) {
@@ -1302,7 +1310,9 @@ int fit_grid(int threads, int path, int grad_mode, int solver, int* grid) {
   constexpr int SE = CSX_NOISE_SEPARABLE, LB = CSX_SOLVER_LBFGS, AT = CSX_SOLVER_ADATOPK;
   const bool ada = solver == AT;
   if (path == M) {
-    if (fit_threads(threads, path) == 128)
+    const int nt = fit_threads(threads, path);
+    if (nt == 64 && !ada) return occupancy_grid<64, M, AD, SE, LB>(grid);
+    if (nt == 128 || nt == 64)
       return ada ? occupancy_grid<128, M, AD, SE, AT>(grid) : occupancy_grid<128, M, AD, SE, LB>(grid);
     return ada ? occupancy_grid<256, M, AD, SE, AT>(grid) : occupancy_grid<256, M, AD, SE, LB>(grid);
   }
@@ -1316,7 +1326,11 @@ static int launch_adjoint(const FitArgs& a, int threads, int grid, cudaStream_t 
   constexpr int HO = CSX_NOISE_HOMOGENEOUS, SE = CSX_NOISE_SEPARABLE, PP = CSX_NOISE_PERPIXEL;
   if (a.path == M) {
     const bool sep = a.noise_kind == SE;
-    if (fit_threads(threads, M) == 128)
+    const int nt = fit_threads(threads, M);
+    if (nt == 64 && SOLVER == CSX_SOLVER_LBFGS)
+      return sep ? launch_one<64, M, AD, SE, SOLVER>(a, grid, s)
+                 : launch_one<64, M, AD, HO, SOLVER>(a, grid, s);
+    if (nt == 128 || nt == 64)
       return sep ? launch_one<128, M, AD, SE, SOLVER>(a, grid, s)
                  : launch_one<128, M, AD, HO, SOLVER>(a, grid, s);
     return sep ? launch_one<256, M, AD, SE, SOLVER>(a, grid, s)
