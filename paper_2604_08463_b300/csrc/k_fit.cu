@@ -275,7 +275,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #else
   const int mst = c.ncell;
 #endif
-  double acc = 0.0;
+  float acc = 0.f;  // per-thread sum over its few cells in FP32, FP64 across the block
   for (int cell = threadIdx.x; cell < c.ncell; cell += NT) {
     const int kd = c.trip[cell], kt = c.trip[c.ncell + cell], ks = c.trip[2 * c.ncell + cell];
     const float* pd = c.tab + kd * NB;
@@ -340,7 +340,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #endif
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
-      acc += (double)nan_f();
+      acc += nan_f();
       continue;
     }
     float v[3][3];
@@ -420,7 +420,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int l = 0; l < 3; ++l) chi += G1[k][l] * Q[l][k] - v[k][l] * AtRA[l][k];
-    acc += (double)chi;
+    acc += chi;
     // W1 = Q Z + C^T N A ;  Psi = M^-1 A^T N (C Z + R N A) = M^-1 (CtA^T Z + AtRA)
     float W1[3][3], Psi[3][3];
     {
@@ -483,7 +483,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       atomicAdd(c.hacc + c.Kd + c.KT + ks, h[2]);
     }
   }
-  return block_sum<NT>(acc, sh.red);
+  return block_sum<NT>((double)acc, sh.red);
 }
 
 // -------------------------------------------------------------------- stream evaluation --------
@@ -663,9 +663,9 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     for (int j = 0; j < count; ++j) {
       const int k = (head - 1 - j + m) % m;
       const float* Sk = c.S + (long long)k * a.Pmax;
-      double dot = 0.0;
-      for (int i = tid; i < P; i += NT) dot += (double)Sk[i] * (double)c.p[i];
-      dot = block_sum<NT>(dot, sh.red);
+      float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
+      for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
+      const double dot = block_sum<NT>((double)dotf, sh.red);
       const double al = sh.rho[k] * dot;
       if (tid == 0) sh.alpha[k] = al;
       const float* Yk = c.Y + (long long)k * a.Pmax;
@@ -675,16 +675,16 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     for (int j = count - 1; j >= 0; --j) {
       const int k = (head - 1 - j + m) % m;
       const float* Yk = c.Y + (long long)k * a.Pmax;
-      double dot = 0.0;
-      for (int i = tid; i < P; i += NT) dot += (double)Yk[i] * (double)c.p[i];
-      dot = block_sum<NT>(dot, sh.red);
+      float dotf = 0.f;
+      for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
+      const double dot = block_sum<NT>((double)dotf, sh.red);
       const double be = sh.rho[k] * dot;
       const float* Sk = c.S + (long long)k * a.Pmax;
       const float coef = (float)(sh.alpha[k] - be);
       for (int i = tid; i < P; i += NT) c.p[i] += coef * Sk[i];
     }
     // negate, mask the active set and outward steps at a bound, directional derivative, QN step
-    double gp = 0.0;
+    float gpf = 0.f;
     float stepn = 0.f;
     for (int i = tid; i < P; i += NT) {
       const int t = ptype(c, i);
@@ -694,16 +694,16 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       float pi = act ? 0.f : -c.p[i];
       if ((c.z[i] <= zl && pi < 0.f) || (c.z[i] >= zu && pi > 0.f)) pi = 0.f;
       c.p[i] = pi;
-      gp += (double)gi * (double)pi;
+      gpf = fmaf(gi, pi, gpf);
       stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
     }
-    gp = block_sum<NT>(gp, sh.red);
+    double gp = block_sum<NT>((double)gpf, sh.red);
     stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
     if (!(gp < 0.0)) {
       // not a descent direction: restart from the projected steepest descent
       count = 0;
       gamma = 1.0;
-      gp = 0.0;
+      gpf = 0.f;
       stepn = 0.f;
       for (int i = tid; i < P; i += NT) {
         const int t = ptype(c, i);
@@ -713,10 +713,10 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         float pi = act ? 0.f : -gi;
         if ((c.z[i] <= zl && pi < 0.f) || (c.z[i] >= zu && pi > 0.f)) pi = 0.f;
         c.p[i] = pi;
-        gp += (double)gi * (double)pi;
+        gpf = fmaf(gi, pi, gpf);
         stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
       }
-      gp = block_sum<NT>(gp, sh.red);
+      gp = block_sum<NT>((double)gpf, sh.red);
       stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
       if (!(gp < 0.0)) {
         status = CSX_FIT_CONVERGED;  // projected gradient vanishes
@@ -786,9 +786,9 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       } else {
         for (int i = tid; i < P; i += NT) c.gt[i] = c.gacc[i] / c.hs[i];
       }
-      double dphi = 0.0;
-      for (int i = tid; i < P; i += NT) dphi += (double)c.gt[i] * (double)c.p[i];
-      dphi = block_sum<NT>(dphi, sh.red);
+      float dphif = 0.f;
+      for (int i = tid; i < P; i += NT) dphif = fmaf(c.gt[i], c.p[i], dphif);
+      const double dphi = block_sum<NT>((double)dphif, sh.red);
       if (!isfinite(ft) || !isfinite(dphi)) {
         a_hi = alpha;
         d_hi = 1.0;
@@ -850,7 +850,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       break;
     }
     // ---- accept: curvature pair and update --------------------------------------------
-    double sy = 0.0, yy = 0.0;
+    float syf = 0.f, yyf = 0.f;
     float sn = 0.f;
     float* Sn = c.S + (long long)head * a.Pmax;
     float* Yn = c.Y + (long long)head * a.Pmax;
@@ -859,12 +859,13 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
       Sn[i] = si;
       Yn[i] = yi;
-      sy += (double)si * (double)yi;
-      yy += (double)yi * (double)yi;
+      syf = fmaf(si, yi, syf);
+      yyf = fmaf(yi, yi, yyf);
       sn = fmaxf(sn, fabsf(si) / c.hs[i] / a.xtol[t]);
       c.z[i] = c.zt[i];
       c.g[i] = c.gt[i];
     }
+    double sy = syf, yy = yyf;
     block_sum2<NT>(sy, yy, sh.red);
     sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
     last_step = sn;
