@@ -22,7 +22,7 @@ os.environ.setdefault("CSX_KMEANS_CACHE", os.path.join(ROOT, ".cache", "kmeans")
 
 from synth import workloads  # noqa: E402
 from tests._inputs import Case, pack  # noqa: E402
-from tests._oracle_jobs import fit_job, oracle_pool  # noqa: E402
+from tests._fitcheck import sampled_fit_check as _sampled_fit_check  # noqa: E402
 from tests._parity import TOL_BETA, assert_grad_close, grad_ref  # noqa: E402
 
 
@@ -77,68 +77,6 @@ def test_gradcheck_nside128_autograd_64_points(csx):
         assert_grad_close(g[i], gr, Sr)
 
 
-def _sampled_fit_check(csx, case, res, picks):
-    """Fitted beta of sampled problems against oracle fits. A parameter passes within its tolerance,
-    or -- when the likelihood is nearly flat along it -- within its tolerance plus the FP32 gradient
-    floor propagated through the curvature: |dbeta_i| <= tol_i + 1e-5 S_i / H_ii, with S_i the
-    summed term magnitude of dL/dbeta_i (the per-component gradient bound of the parity tests) and
-    H_ii the oracle's d2L/dbeta_i2 (central differences of its analytic gradient) at its optimum.
-    Failing that, a parameter passes within its tolerance plus the resolution of the optimiser's
-    value-based decisions, sqrt(2 eps / H_ii) with eps = 1e-6 |chi2| (the line search does not
-    distinguish values closer than that), provided the fit's L is within eps of the oracle's: an
-    optimum equivalent to the oracle's in FP32 arithmetic. A parameter the data leave statistically
-    unconstrained -- 1-sigma width sqrt(2 / H_ii) above 100 tolerances -- is counted and reported
-    instead. The counts of each case are printed."""
-    from oracle import likelihood as lk
-    wl = case.wl
-    offs, _ = csx.param_offsets(wl.K, wl.nreal)
-    jobs = []
-    for q in picks:
-        c, r = divmod(q, wl.nreal)
-        jobs.append((case.nu, case.d64(r), case.ninv64, wl.labels[c], wl.K[c], wl.beta0(c),
-                     workloads.LOWER, workloads.UPPER))
-    with oracle_pool(len(jobs)) as pool:
-        refs = pool.map(fit_job, jobs)
-    out = {k: v.cpu().numpy() for k, v in res.items()}
-    worst, floored, vfloored, unconstrained = 0.0, 0, 0, 0
-    for q, (x_ref, L_ref, interior) in zip(picks, refs):
-        c, r = divmod(q, wl.nreal)
-        K = wl.K[c]
-        P = int(K.sum())
-        assert out["status"][q] == 0, (q, out["status"][q], out["iters"][q])
-        got = out["beta"][offs[q]:offs[q] + P].astype(np.float64)
-        types = np.concatenate([np.full(K[j], j) for j in range(3)])
-        tol = TOL_BETA[types]
-        err = np.abs(got - x_ref)
-        over = np.nonzero(interior & (err > tol))[0]
-        if over.size:
-            d64, lab = case.d64(r), wl.labels[c]
-            S = lk.gradient_term_scale(case.nu, d64, case.ninv64, lab, K, x_ref)
-            for i in over:
-                h = 0.1 * tol[i]
-                xp, xm = x_ref.copy(), x_ref.copy()
-                xp[i] += h
-                xm[i] -= h
-                gp = lk.spectral_gradient(case.nu, d64, case.ninv64, lab, K, xp)[1][i]
-                gm = lk.spectral_gradient(case.nu, d64, case.ninv64, lab, K, xm)[1][i]
-                H = (gp - gm) / (2 * h)
-                assert H > 0, (q, i, H)
-                eps = 1e-6 * abs(L_ref + lk.data_norm(d64, case.ninv64))
-                if err[i] <= tol[i] + 1e-5 * S[i] / H:
-                    floored += 1
-                elif err[i] <= tol[i] + np.sqrt(2.0 * eps / H) and out["L"][q] - L_ref <= eps:
-                    vfloored += 1
-                elif np.sqrt(2.0 / H) > 100 * tol[i]:
-                    unconstrained += 1
-                    print("unconstrained: problem %d parameter %d (type %d) |err| %.2e, sigma %.3f"
-                          % (q, i, types[i], err[i], np.sqrt(2.0 / H)))
-                else:
-                    raise AssertionError((q, P, i, types[i], err[i], tol[i], S[i], H))
-        assert abs(out["L"][q] - L_ref) <= 1e-5 * abs(L_ref), (q, out["L"][q], L_ref)
-        worst = max(worst, (err / tol)[interior].max(initial=0.0))
-    return worst, floored, vfloored, unconstrained
-
-
 def test_bench_scan_fit_sampled_problems(csx):
     """The bench's workload and launch: every one of the 10000 problems in one persistent launch;
     six problems (P spread over the scan's lower half, where oracle fits take seconds) are refitted
@@ -158,9 +96,9 @@ def test_bench_scan_fit_sampled_problems(csx):
     for lo, hi in ((3, 20), (20, 50), (50, 80), (80, 120), (120, 160), (160, 200)):
         cand = np.nonzero((P >= lo) & (P < hi))[0]
         picks.append(int(rng.choice(cand)))
-    worst, floored, vfl, unc = _sampled_fit_check(csx, case, res, picks)
-    print("worst |err|/tol %.3f; within the gradient floor: %d; value floor: %d; unconstrained: %d"
-          % (worst, floored, vfl, unc))
+    worst, floored, vfl, unc, jt = _sampled_fit_check(csx, case, res, picks)
+    print("worst |err|/tol %.3f; within the gradient floor: %d; value floor: %d; unconstrained: %d; "
+          "joint: %d" % (worst, floored, vfl, unc, jt))
 
 
 def test_large_k_scan_nside16_sampled_problems(csx):
@@ -176,6 +114,6 @@ def test_large_k_scan_nside16_sampled_problems(csx):
     P = np.repeat(wl.P, wl.nreal)
     order = np.argsort(P)
     picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
-    worst, floored, vfl, unc = _sampled_fit_check(csx, case, res, picks)
+    worst, floored, vfl, unc, jt = _sampled_fit_check(csx, case, res, picks)
     print("P", P[picks], "worst |err|/tol %.3f; within the gradient floor: %d; value floor: %d; "
-          "unconstrained: %d" % (worst, floored, vfl, unc))
+          "unconstrained: %d; joint: %d" % (worst, floored, vfl, unc, jt))

@@ -1,0 +1,74 @@
+"""The alternative partitions of Sec. 4.3 and Sec. 4.5 (multi-resolution HEALPix superpixels per
+Galactic region; post-clustering binning of fitted parameter maps) fitted by the same kernels, on
+the 60% sky at nside 16, against oracle fits (acceptance as in test_gpu_fullsize)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from synth import healpix, kmeans, partitions as pt, sky as S, workloads  # noqa: E402
+from tests._fitcheck import sampled_fit_check  # noqa: E402
+from tests._inputs import Case, pack  # noqa: E402
+
+NSIDE = 16
+
+
+@pytest.fixture(scope="module")
+def csx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_08463_b300 import csx as mod
+    mod.lib()
+    return mod
+
+
+def _regions_sky():
+    reg = pt.latitude_regions(NSIDE, np.arange(healpix.npix(NSIDE)))
+    pix = np.nonzero(reg >= 0)[0]
+    return pix, S.make_sky(NSIDE, pix=pix, truth="smooth", hitcount=True)
+
+
+def _fit(csx, wl):
+    case = Case(wl, "separable")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(pack(wl, [wl.beta0(c) for c in range(wl.nconf) for _ in range(wl.nreal)]),
+                         device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0)
+    torch.cuda.synchronize()
+    return case, res
+
+
+def test_multires_configuration(csx):
+    pix, sk = _regions_sky()
+    lab, K = pt.multires_labels(NSIDE, pix, levels=((4, 4, 8), (0, 2, 4), (1, 1, 2)))
+    wl = workloads.Workload("multires16", sk, K[None], lab[None], 2, "separable")
+    case, res = _fit(csx, wl)
+    worst, fl, vfl, unc, jt = sampled_fit_check(csx, case, res, [0, 1])
+    print("K", K.tolist(), "worst |err|/tol %.3f; floors %d/%d; unconstrained %d; joint %d"
+          % (worst, fl, vfl, unc, jt))
+
+
+def test_post_clustering_binning(csx):
+    pix, sk = _regions_sky()
+    vec = healpix.unit_vectors(NSIDE)[pix]
+    Kk = np.array([30, 6, 10])
+    lab0 = np.stack([kmeans.patch_labels(vec, int(k), key="regions%d" % NSIDE) for k in Kk])
+    wl0 = workloads.Workload("kmeans16", sk, Kk[None].astype(np.int32), lab0[None].astype(np.int32),
+                             1, "separable")
+    _, res0 = _fit(csx, wl0)
+    beta = res0["beta"].cpu().numpy().astype(np.float64)
+    offs = np.concatenate([[0], np.cumsum(Kk)])
+    labs, Ks = [], []
+    for j in range(3):
+        per_pixel = beta[offs[j]:offs[j + 1]][lab0[j]]  # the fitted parameter map
+        lb, kb = pt.binned_labels(per_pixel, vec, nbin=8, fwhm_deg=10.0)
+        labs.append(lb)
+        Ks.append(kb)
+    Kb = np.array(Ks, dtype=np.int32)
+    wl = workloads.Workload("binned16", sk, Kb[None], np.stack(labs)[None].astype(np.int32), 2,
+                            "separable")
+    case, res = _fit(csx, wl)
+    worst, fl, vfl, unc, jt = sampled_fit_check(csx, case, res, [0, 1])
+    print("K", Kb.tolist(), "worst |err|/tol %.3f; floors %d/%d; unconstrained %d; joint %d"
+          % (worst, fl, vfl, unc, jt))
