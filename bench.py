@@ -37,9 +37,9 @@ BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12  # residual moments (R, C, Q) + ce
 FLOPS_PER_CELL_EVAL = 4600   # FP32 operations of one cell's chi2 + gradient (FMA = 2)
 FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (FMA = 2)
 # DRAM bytes (read + write) per unit from the committed ncu captures (profiles/): the persistent
-# fit per cell evaluation (1000-problem scan, 46.6 M cell evaluations, scaled by units), the
+# fit per cell evaluation (1000-problem scan, 47.2 M cell evaluations, scaled by units), the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
-TRAFFIC_FIT_PER_CELL_EVAL = 1054.0
+TRAFFIC_FIT_PER_CELL_EVAL = 979.5
 TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.5, "L": 129.5}
 
 
@@ -365,6 +365,8 @@ def run_csx(args):
 
     streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
     kmeans_gpu = kmeans_rates(csx, inp) if (rank == 0 and not args.no_kmeans) else None
+    spectra = (spectra_rates(csx, inp, model, sky, labels, fg, res["beta"])
+               if (rank == 0 and not args.no_spectra) else None)
 
     # end to end: pinned host inputs -> device, step, results -> host
     e2e = None
@@ -475,6 +477,7 @@ def run_csx(args):
         "streaming_kernel": streaming,
         "adatopk_fit": ada,
         "kmeans": kmeans_gpu,
+        "residual_spectra": spectra,
         "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
@@ -576,6 +579,60 @@ def kmeans_rates(csx, inp):
             "timing": "CUDA events around one csx_kmeans launch (one CTA per labeling)"}
 
 
+SPECTRA = {"nconf": 100, "lmax": 150}
+SM_MAX_MHZ = 2032.0
+
+
+def spectra_rates(csx, inp, model, sky, labels, fg, beta, ncall=5):
+    """Residual spectra (Sec. 2.5) of the first 100 configurations x their realizations at the
+    step's fitted parameters: s_hat and r_sys from the reconstruction kernel (untimed), then the
+    total, systematic and statistical (EE, BB) pseudo-spectra to l = 150 on the cut sky, each
+    averaged over realizations; CUDA events around `ncall` repetitions of the three calls."""
+    import numpy as np
+    import torch
+    wl = inp["wl"]
+    nconf, nreal, lmax = SPECTRA["nconf"], wl.nreal, SPECTRA["lmax"]
+    K = inp["K"][:nconf]
+    offs, _ = csx.param_offsets(inp["K"], nreal)
+    b = beta[:int(offs[nconf * nreal])].contiguous()
+    rec = csx.reconstruct(model, sky, labels[:nconf].contiguous(), K, b, d_fg=fg, s_hat=True,
+                          r_sys=True, metrics=False)
+    dev = beta.device
+    s_true = torch.tensor(np.asarray(wl.sky.cmb, dtype=np.float32), device=dev)
+    plan = csx.ShtPlan(SCAN["nside"], lmax, wl.sky.pix)
+    out = csx.residual_spectra(plan, rec["s_hat"], s_true, rec["r_sys"], nreal)  # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(ncall):
+        out = csx.residual_spectra(plan, rec["s_hat"], s_true, rec["r_sys"], nreal)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / ncall
+    maps = 3 * nconf * nreal
+    # algorithmic FP32 work per map: ring sums 2 x (real x complex) per (pixel, m); harmonic sums
+    # 4 x (real x complex) per (ring, l, m)
+    from synth import healpix
+    zc, _ = healpix.pixel_centres(SCAN["nside"])
+    nring = np.unique(zc[np.asarray(wl.sky.pix)]).size
+    nlm = sum(lmax - max(m, 2) + 1 for m in range(lmax + 1) if max(m, 2) <= lmax)
+    flops = maps * (8.0 * wl.npix * (lmax + 1) + 16.0 * nring * nlm)
+    peak = fp32_peak_tflops(SM_MAX_MHZ)
+    tf = flops / (ms * 1e-3) / 1e12
+    bb = out["stat"][:, 1, 2:].cpu().numpy()
+    del rec, out
+    torch.cuda.empty_cache()
+    return {"configurations": nconf, "realizations": nreal, "lmax": lmax, "maps_per_call": maps,
+            "ms": ms, "maps_per_s": maps / (ms * 1e-3),
+            "stat_bb_mean_l2_150": float(bb.mean()),
+            "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf / peak,
+                         "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (148 x 128 x 2 x 2032 MHz)"},
+            "timing": "CUDA events around %d x (tot, syst, stat) residual_spectra calls" % ncall}
+
+
 def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fits_per_s):
     """Plain GPU form: the same optimiser with central finite-difference gradients of the forward
     likelihood (2P+1 evaluations per gradient), on 20 configurations spanning the P range."""
@@ -591,10 +648,14 @@ def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fit
                       dtype=torch.float32, device=labels.device)
     max_iter = 10
     torch.cuda.synchronize()
-    t0 = time.time()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     res = csx.fit_batch(model, sky, sub_lab, K, b0, grad_mode="fd", path="stream", max_iter=max_iter)
+    e1.record(stream)
     torch.cuda.synchronize()
-    wall = time.time() - t0
+    wall = e0.elapsed_time(e1) * 1e-3  # device time of the launch (CUDA events)
     it = res["iters"].cpu().numpy()
     ne = res["nevals"].cpu().numpy()
     # time per quasi-Newton iteration of the plain form, scaled to the adjoint fit's iteration count
@@ -604,9 +665,9 @@ def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fit
     fits_per_s = nprob / extrap_fit_s
     return {"subset": "%d configurations (P quantiles %d..%d) x %d realizations, max_iter %d"
                       % (len(pick), int(P[pick].min()), int(P[pick].max()), wl.nreal, max_iter),
-            "wall_s": wall, "iters_mean": float(it.mean()), "evals_mean": float(ne.mean()),
+            "device_s": wall, "iters_mean": float(it.mean()), "evals_mean": float(ne.mean()),
             "fits_per_s_extrapolated": fits_per_s,
-            "extrapolation": "subset wall time per iteration x the adjoint fit's mean iterations "
+            "extrapolation": "subset device time per iteration x the adjoint fit's mean iterations "
                              "(%.1f); the subset's P mix differs from the full scan" % adj_iters,
             "adjoint_speedup": adj_fits_per_s / fits_per_s}
 
@@ -658,6 +719,7 @@ def main():
     ap.add_argument("--no-stream", action="store_true", help="skip the streaming-kernel rates")
     ap.add_argument("--no-adatopk", action="store_true", help="skip the AdaTopK comparison fit")
     ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU K-means rates")
+    ap.add_argument("--no-spectra", action="store_true", help="skip the residual-spectra rates")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

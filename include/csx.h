@@ -258,6 +258,44 @@ int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot
 int csx_kmeans(const double* vec, int32_t n, int32_t nlab, const int32_t* K, const int32_t* init,
                int32_t max_iter, int32_t* labels, int32_t* iters, void* stream);
 
+/*
+ * Pseudo-C_ell spectra of polarisation maps (Sec. 2.5: the residual spectra C_ell^tot, C_ell^syst
+ * = C^BB([W d_fg]_CMB) and C_ell^stat = <C^BB([s_hat - s_true] - [W d_fg]_CMB)>_n are pseudo-spectra
+ * of residual maps on the observed sky). Conventions: spin-weighted harmonics sY_lm of Goldberg
+ * et al. (1967); (Q +- iU) = sum a_{+-2,lm} (+-2)Y_lm; a^E = -(a_2 + a_-2)/2, a^B = i(a_2 - a_-2)/2;
+ * a_{+-2,lm} = (4 pi / (12 nside^2)) sum over the observed pixels of (Q +- iU) conj((+-2)Y_lm) (the
+ * map is zero elsewhere; no f_sky division); C_l = (|a_l0|^2 + 2 sum_{m>0} |a_lm|^2) / (2l + 1);
+ * C_0 = C_1 = 0.
+ *
+ * A plan holds the geometry of the observed pixels and the spin-2 harmonic tables of its rings
+ * (float32, nring x ~lmax^2/2 x 8 bytes, computed on the device in float64).
+ *   nside: 1 .. 1024; lmax: 0 .. 4 nside - 1 (and <= 1023)
+ *   pix:   HOST int32 [npix], RING pixel indices, strictly increasing, in [0, 12 nside^2)
+ *   plan:  receives the plan (owned by the caller; csx_sht_plan_destroy frees it)
+ * The plan belongs to the current device and is used on it only. Errors: CSX_EINVAL for bad sizes
+ * or an unsorted / out-of-range pix; CSX_ECUDA / CSX_ENOMEM. The call synchronises `stream`.
+ */
+typedef struct csx_sht_plan csx_sht_plan;
+int csx_sht_plan_create(int32_t nside, int32_t lmax, const int32_t* pix, int32_t npix,
+                        csx_sht_plan** plan, void* stream);
+int csx_sht_plan_destroy(csx_sht_plan* plan);
+
+/*
+ * (EE, BB) pseudo-spectra of nmaps maps, averaged over consecutive groups of navg maps:
+ *   map b, observed pixel p, Stokes k (0 = Q, 1 = U):
+ *     X_b[p][k] = maps[b * map_stride + p * pix_stride + k * pol_stride]
+ *                 - sub_common[2 p + k] (if not NULL) - sub_each[(b * npix + p) * 2 + k] (if not NULL)
+ *   e.g. the CMB residual of csx_reconstruct's s_hat: map_stride = 6 npix, pix_stride = 6,
+ *   pol_stride = 3, sub_common = s_true [npix][2], sub_each = r_sys [nmaps][npix][2] (for stat).
+ *   maps, sub_common, sub_each: device float (4-byte aligned); strides in elements, >= 0
+ *   cl:    device double [nmaps / navg][2][lmax + 1] (EE, BB), overwritten; navg >= 1 divides nmaps
+ * Scratch: about min(nmaps, 256) x nring x (lmax + 1) x 16 bytes. Asynchronous on `stream`.
+ * Errors: CSX_EINVAL for a NULL plan / maps / cl, bad sizes or misaligned pointers.
+ */
+int csx_pseudo_cl(const csx_sht_plan* plan, int32_t nmaps, const float* maps, int64_t map_stride,
+                  int32_t pix_stride, int32_t pol_stride, const float* sub_common,
+                  const float* sub_each, int32_t navg, double* cl, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

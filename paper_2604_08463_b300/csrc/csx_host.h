@@ -30,6 +30,7 @@ enum ScratchId {
   SCR_MISC,         // small counters
   SCR_RECON_DESC,
   SCR_KMEANS,       // K-means: per-labeling best dot products, cluster counts and offsets
+  SCR_SHT,          // pseudo-C_ell: ring coefficients of a chunk of maps
   SCR_COUNT
 };
 void* scratch(ScratchId id, size_t bytes, int* err);

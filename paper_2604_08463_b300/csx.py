@@ -24,7 +24,8 @@ M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
            "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_noalloc",
-           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select", "csx_kmeans"]
+           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select", "csx_kmeans",
+           "csx_sht_plan_create", "csx_sht_plan_destroy", "csx_pseudo_cl"]
 
 
 class CsxError(RuntimeError):
@@ -78,6 +79,9 @@ def lib():
                                       vp, vp, vp, vp]
         L.csx_select.argtypes = [i32, i32, vp, vp, vp, vp]
         L.csx_kmeans.argtypes = [vp, i32, i32, pi32, vp, i32, vp, vp, vp]
+        L.csx_sht_plan_create.argtypes = [i32, i32, pi32, i32, POINTER(c_void_p), vp]
+        L.csx_sht_plan_destroy.argtypes = [vp]
+        L.csx_pseudo_cl.argtypes = [vp, i32, vp, ctypes.c_int64, i32, i32, vp, vp, i32, vp, vp]
         for name in EXPORTS:
             if name not in ("csx_version", "csx_last_error"):
                 getattr(L, name).restype = i32
@@ -325,6 +329,69 @@ def kmeans(vec: torch.Tensor, K, init, max_iter: int = 30):
     _check(lib().csx_kmeans(_ptr(vec), n, int(Kh.size), Kp, _ptr(init_d), int(max_iter),
                             _ptr(labels), _ptr(iters), _stream()))
     return labels, iters
+
+
+class ShtPlan:
+    """Ring geometry and spin-2 harmonic tables of the observed pixels `pix` (RING, nside) up to
+    lmax, on the current CUDA device (csx_sht_plan_create; freed with the object)."""
+
+    def __init__(self, nside: int, lmax: int, pix):
+        pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int32).reshape(-1))
+        self.nside, self.lmax, self.npix = int(nside), int(lmax), int(pix.size)
+        self._pix = pix
+        h = c_void_p()
+        _check(lib().csx_sht_plan_create(self.nside, self.lmax,
+                                         pix.ctypes.data_as(POINTER(c_int32)), self.npix,
+                                         ctypes.byref(h), _stream()))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().csx_sht_plan_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pseudo_cl(plan: ShtPlan, maps: torch.Tensor, sub_common=None, sub_each=None, navg: int = 1):
+    """(EE, BB) pseudo-spectra [nmaps // navg, 2, lmax + 1] (float64) of the Q, U maps
+    maps[b, p, k] (k = 0 Q, 1 U; any strides in the last two dims, e.g. s_hat[..., 0] of
+    `reconstruct`), minus sub_common [npix, 2] and sub_each [nmaps, npix, 2] when given, averaged
+    over consecutive groups of navg maps."""
+    if maps.dim() != 3 or maps.shape[1] != plan.npix or maps.shape[2] != 2:
+        raise ValueError("maps must be [nmaps, npix, 2]")
+    if maps.dtype != torch.float32:
+        raise ValueError("maps must be float32")
+    nmaps = maps.shape[0]
+    if sub_common is not None:
+        sub_common = sub_common.to(torch.float32).contiguous()
+    if sub_each is not None:
+        sub_each = sub_each.to(torch.float32).contiguous()
+    if not maps.is_cuda:
+        raise ValueError("maps must be a CUDA tensor")
+    st = maps.stride()
+    cl = torch.empty((nmaps // max(navg, 1), 2, plan.lmax + 1), dtype=torch.float64,
+                     device=maps.device)
+    _check(lib().csx_pseudo_cl(plan._h, nmaps, c_void_p(maps.data_ptr()), st[0], st[1], st[2],
+                               _ptr(sub_common),
+                               _ptr(sub_each), int(navg), _ptr(cl), _stream()))
+    return cl
+
+
+def residual_spectra(plan: ShtPlan, s_hat: torch.Tensor, s_true: torch.Tensor, r_sys, nreal: int):
+    """The residual spectra of Sec. 2.5 for every configuration, averaged over its nreal noise
+    realizations: s_hat [nprob, npix, 2, 3] and r_sys [nprob, npix, 2] of `reconstruct` (problem
+    q = c * nreal + n), s_true [npix, 2] the input CMB. Returns {'tot', 'syst', 'stat'}, each
+    [nconf, 2, lmax + 1] (EE, BB)."""
+    cmb = s_hat[..., 0]
+    r_sys = r_sys.contiguous()
+    return {"tot": pseudo_cl(plan, cmb, sub_common=s_true, navg=nreal),
+            "syst": pseudo_cl(plan, r_sys, navg=nreal),
+            "stat": pseudo_cl(plan, cmb, sub_common=s_true, sub_each=r_sys, navg=nreal)}
 
 
 def chunk(n: int, world: int, rank: int):

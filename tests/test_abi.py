@@ -102,3 +102,25 @@ def test_misaligned_pointers_are_rejected_on_the_host(lib):
                                        K, 1, ctypes.c_void_p(ok16 + 1), ctypes.c_void_p(ok16),
                                        ctypes.c_void_p(ok16), None)
     assert rc == -1 and b"beta must be 4-byte aligned" in lib.csx_last_error()
+
+
+def test_spectra_arguments_are_refused_on_the_host(lib):
+    """The pseudo-C_ell entry points check sizes and the pixel list before touching a device."""
+    import ctypes
+    plan = ctypes.c_void_p()
+    pix = (ctypes.c_int32 * 4)(0, 5, 5, 9)
+    rc = lib.csx_sht_plan_create(4, 11, pix, 4, ctypes.byref(plan), None)
+    assert rc == -1 and b"strictly increasing" in lib.csx_last_error() and not plan.value
+    pix = (ctypes.c_int32 * 2)(0, 192)
+    rc = lib.csx_sht_plan_create(4, 11, pix, 2, ctypes.byref(plan), None)
+    assert rc == -1 and b"pix out of range" in lib.csx_last_error()
+    rc = lib.csx_sht_plan_create(4, 16, pix, 1, ctypes.byref(plan), None)
+    assert rc == -1 and b"lmax" in lib.csx_last_error()
+    rc = lib.csx_sht_plan_create(0, 0, pix, 1, ctypes.byref(plan), None)
+    assert rc == -1 and b"nside" in lib.csx_last_error()
+    rc = lib.csx_sht_plan_create(4, 11, pix, 1, None, None)
+    assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
+    rc = lib.csx_pseudo_cl(None, 1, ctypes.c_void_p(0x10000), 2, 2, 1, None, None, 1,
+                           ctypes.c_void_p(0x10000), None)
+    assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
+    assert lib.csx_sht_plan_destroy(None) == 0
