@@ -591,10 +591,11 @@ def spectra_rates(csx, inp, model, sky, labels, fg, beta, ncall=5):
     import numpy as np
     import torch
     wl = inp["wl"]
-    nconf, nreal, lmax = SPECTRA["nconf"], wl.nreal, SPECTRA["lmax"]
+    nconf, nreal, lmax = min(SPECTRA["nconf"], wl.nconf), wl.nreal, SPECTRA["lmax"]
     K = inp["K"][:nconf]
     offs, _ = csx.param_offsets(inp["K"], nreal)
-    b = beta[:int(offs[nconf * nreal])].contiguous()
+    nq = nconf * nreal
+    b = beta[:int(offs[nq]) if nq < len(offs) else beta.numel()].contiguous()
     rec = csx.reconstruct(model, sky, labels[:nconf].contiguous(), K, b, d_fg=fg, s_hat=True,
                           r_sys=True, metrics=False)
     dev = beta.device

@@ -4,8 +4,9 @@
  * C ABI of the hot path of the parametric spectral-likelihood method of arxiv 2604.08463:
  * the mixing matrix (Eq. 5), the clustered spectral likelihood (Eq. 4 over the patches of
  * Sec. 2.2), its adjoint gradient (Sec. 3.3.1), the batched box-bounded fit over patch
- * configurations x noise realizations (Eq. 7, Sec. 3.1, App. A), and the reconstruction
- * s_hat = W d with its residual diagnostics (Eqs. 3, 8-11, 14-15).
+ * configurations x noise realizations (Eq. 7, Sec. 3.1, App. A), the reconstruction
+ * s_hat = W d with its residual diagnostics (Eqs. 3, 8-11, 14-15), the pseudo-C_ell residual
+ * spectra (Sec. 2.5) and the seeded spherical K-means patches (Sec. 2.2).
  *
  * Conventions shared by every call
  *   - Plain pointers and sizes only. "device" pointers are CUDA device memory of the current
@@ -295,6 +296,22 @@ int csx_sht_plan_destroy(csx_sht_plan* plan);
 int csx_pseudo_cl(const csx_sht_plan* plan, int32_t nmaps, const float* maps, int64_t map_stride,
                   int32_t pix_stride, int32_t pol_stride, const float* sub_common,
                   const float* sub_each, int32_t navg, double* cl, void* stream);
+
+/*
+ * The three residual spectra of Sec. 2.5 in one pass: per problem q the CMB residual
+ * X_q = s_hat_q - s_true (read through the strides of csx_pseudo_cl, e.g. csx_reconstruct's s_hat:
+ * map_stride = 6 npix, pix_stride = 6, pol_stride = 3) and the foreground leakage Y_q = r_sys_q;
+ * their ring coefficients are taken once each and the statistical residual uses
+ * a_lm(X - Y) = a_lm(X) - a_lm(Y). Averaged over groups of navg problems (the realizations):
+ *   cl_tot = <C(X)>, cl_syst = <C(Y)>, cl_stat = <C(X - Y)>, each device double
+ *   [nprob / navg][2][lmax + 1] (EE, BB), overwritten.
+ *   s_hat: device float; s_true: device float [npix][2] or NULL (no subtraction);
+ *   r_sys: device float [nprob][npix][2]. Errors as csx_pseudo_cl. Asynchronous on `stream`.
+ */
+int csx_residual_cl(const csx_sht_plan* plan, int32_t nprob, const float* s_hat,
+                    int64_t map_stride, int32_t pix_stride, int32_t pol_stride,
+                    const float* s_true, const float* r_sys, int32_t navg, double* cl_tot,
+                    double* cl_syst, double* cl_stat, void* stream);
 
 #ifdef __cplusplus
 }

@@ -25,7 +25,7 @@ M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
            "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_noalloc",
            "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select", "csx_kmeans",
-           "csx_sht_plan_create", "csx_sht_plan_destroy", "csx_pseudo_cl"]
+           "csx_sht_plan_create", "csx_sht_plan_destroy", "csx_pseudo_cl", "csx_residual_cl"]
 
 
 class CsxError(RuntimeError):
@@ -82,6 +82,8 @@ def lib():
         L.csx_sht_plan_create.argtypes = [i32, i32, pi32, i32, POINTER(c_void_p), vp]
         L.csx_sht_plan_destroy.argtypes = [vp]
         L.csx_pseudo_cl.argtypes = [vp, i32, vp, ctypes.c_int64, i32, i32, vp, vp, i32, vp, vp]
+        L.csx_residual_cl.argtypes = [vp, i32, vp, ctypes.c_int64, i32, i32, vp, vp, i32, vp, vp,
+                                      vp, vp]
         for name in EXPORTS:
             if name not in ("csx_version", "csx_last_error"):
                 getattr(L, name).restype = i32
@@ -386,12 +388,22 @@ def residual_spectra(plan: ShtPlan, s_hat: torch.Tensor, s_true: torch.Tensor, r
     """The residual spectra of Sec. 2.5 for every configuration, averaged over its nreal noise
     realizations: s_hat [nprob, npix, 2, 3] and r_sys [nprob, npix, 2] of `reconstruct` (problem
     q = c * nreal + n), s_true [npix, 2] the input CMB. Returns {'tot', 'syst', 'stat'}, each
-    [nconf, 2, lmax + 1] (EE, BB)."""
-    cmb = s_hat[..., 0]
-    r_sys = r_sys.contiguous()
-    return {"tot": pseudo_cl(plan, cmb, sub_common=s_true, navg=nreal),
-            "syst": pseudo_cl(plan, r_sys, navg=nreal),
-            "stat": pseudo_cl(plan, cmb, sub_common=s_true, sub_each=r_sys, navg=nreal)}
+    [nconf, 2, lmax + 1] (EE, BB). One pass: the ring coefficients of s_hat - s_true and of r_sys
+    are taken once and a_lm of their difference is the difference of theirs."""
+    if s_hat.dim() != 4 or s_hat.shape[1] != plan.npix or s_hat.shape[2:] != (2, 3):
+        raise ValueError("s_hat must be [nprob, npix, 2, 3]")
+    if s_hat.dtype != torch.float32 or not s_hat.is_cuda:
+        raise ValueError("s_hat must be a float32 CUDA tensor")
+    nprob = s_hat.shape[0]
+    r_sys = r_sys.to(torch.float32).contiguous()
+    s_true = s_true.to(torch.float32).contiguous() if s_true is not None else None
+    st = s_hat.stride()
+    out = {k: torch.empty((nprob // max(nreal, 1), 2, plan.lmax + 1), dtype=torch.float64,
+                          device=s_hat.device) for k in ("tot", "syst", "stat")}
+    _check(lib().csx_residual_cl(plan._h, nprob, c_void_p(s_hat.data_ptr()), st[0], st[1], st[2],
+                                 _ptr(s_true), _ptr(r_sys), int(nreal), _ptr(out["tot"]),
+                                 _ptr(out["syst"]), _ptr(out["stat"]), _stream()))
+    return out
 
 
 def chunk(n: int, world: int, rank: int):

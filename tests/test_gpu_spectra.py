@@ -146,3 +146,22 @@ def test_residual_spectra_of_reconstructed_maps(csx):
         ref = osp.residual_spectra(16, wl.sky.pix, sh[sl], st, rs[sl], lmax)
         for k in ("tot", "syst", "stat"):
             _close(got[k][c].cpu().numpy(), ref[k])
+
+
+def test_fused_residual_spectra_equal_three_pseudo_cl_calls(csx):
+    """One pass (ring coefficients of s_hat - s_true and of r_sys, a_lm of the difference as the
+    difference) against three separate spectra calls, 10 problems in groups of 5, nside 16."""
+    nside, lmax = 16, 40
+    pix = _masked(nside, 0.8, 7)
+    rng = np.random.default_rng(8)
+    s_hat = torch.from_numpy(rng.normal(size=(10, pix.size, 2, 3)).astype(np.float32)).cuda()
+    s_true = torch.from_numpy(rng.normal(size=(pix.size, 2)).astype(np.float32)).cuda()
+    r_sys = torch.from_numpy((0.2 * rng.normal(size=(10, pix.size, 2))).astype(np.float32)).cuda()
+    plan = csx.ShtPlan(nside, lmax, pix)
+    got = csx.residual_spectra(plan, s_hat, s_true, r_sys, nreal=5)
+    cmb = s_hat[..., 0]
+    ref = {"tot": csx.pseudo_cl(plan, cmb, sub_common=s_true, navg=5),
+           "syst": csx.pseudo_cl(plan, r_sys, navg=5),
+           "stat": csx.pseudo_cl(plan, cmb, sub_common=s_true, sub_each=r_sys, navg=5)}
+    for k in ref:
+        _close(got[k].cpu().numpy(), ref[k].cpu().numpy())
