@@ -587,7 +587,7 @@ def spectra_rates(csx, inp, model, sky, labels, fg, beta, ncall=5):
     """Residual spectra (Sec. 2.5) of the first 100 configurations x their realizations at the
     step's fitted parameters: s_hat and r_sys from the reconstruction kernel (untimed), then the
     total, systematic and statistical (EE, BB) pseudo-spectra to l = 150 on the cut sky, each
-    averaged over realizations; CUDA events around `ncall` repetitions of the three calls."""
+    averaged over realizations, in one pass per call; CUDA events around `ncall` calls."""
     import numpy as np
     import torch
     wl = inp["wl"]
@@ -612,26 +612,28 @@ def spectra_rates(csx, inp, model, sky, labels, fg, beta, ncall=5):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / ncall
-    maps = 3 * nconf * nreal
-    # algorithmic FP32 work per map: ring sums 2 x (real x complex) per (pixel, m); harmonic sums
-    # 4 x (real x complex) per (ring, l, m)
+    nprob = nconf * nreal
+    # algorithmic FP32 work: two transforms per problem (s_hat - s_true and r_sys; the statistical
+    # residual's coefficients are their difference): ring sums 2 x (real x complex) per (pixel, m),
+    # harmonic sums 4 x (real x complex) per (ring, l, m)
     from synth import healpix
     zc, _ = healpix.pixel_centres(SCAN["nside"])
     nring = np.unique(zc[np.asarray(wl.sky.pix)]).size
     nlm = sum(lmax - max(m, 2) + 1 for m in range(lmax + 1) if max(m, 2) <= lmax)
-    flops = maps * (8.0 * wl.npix * (lmax + 1) + 16.0 * nring * nlm)
+    flops = 2 * nprob * (8.0 * wl.npix * (lmax + 1) + 16.0 * nring * nlm)
     peak = fp32_peak_tflops(SM_MAX_MHZ)
     tf = flops / (ms * 1e-3) / 1e12
     bb = out["stat"][:, 1, 2:].cpu().numpy()
     del rec, out
     torch.cuda.empty_cache()
-    return {"configurations": nconf, "realizations": nreal, "lmax": lmax, "maps_per_call": maps,
-            "ms": ms, "maps_per_s": maps / (ms * 1e-3),
+    return {"configurations": nconf, "realizations": nreal, "lmax": lmax, "problems_per_call": nprob,
+            "transforms_per_call": 2 * nprob, "ms": ms, "problems_per_s": nprob / (ms * 1e-3),
             "stat_bb_mean_l2_150": float(bb.mean()),
             "roofline": {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                          "frac": tf / peak,
                          "peak_source": "FP32 FMA lanes x SMs x 2 x max SM clock (148 x 128 x 2 x 2032 MHz)"},
-            "timing": "CUDA events around %d x (tot, syst, stat) residual_spectra calls" % ncall}
+            "timing": "CUDA events around %d residual_spectra calls (tot, syst, stat of every "
+                      "configuration)" % ncall}
 
 
 def plain_form(csx, model, sky, labels, inp, adj_ms_per_iter, adj_iters, adj_fits_per_s):
