@@ -298,17 +298,12 @@ def test_fit_small_scan(path):
                          device="cuda")
     res = csx.fit_batch(model, sky, labels, wl.K, beta0, path=path)
     torch.cuda.synchronize()
-    out = {k: v.cpu().numpy() for k, v in res.items()}
-    offs, _ = csx.param_offsets(wl.K, wl.nreal)
-    worst = 0.0
-    for c in range(wl.nconf):
-        for r in range(wl.nreal):
-            q = c * wl.nreal + r
-            assert out["status"][q] == 0, (q, out["status"][q], out["iters"][q])
-            ratio, L_ref = _check_fit(case, out, c, r, offs[q])
-            worst = max(worst, ratio.max())
-            assert abs(out["L"][q] - L_ref) <= 1e-5 * abs(L_ref)
-    print("worst |err|/tol", worst)
+    # every problem; a parameter outside its tolerance is judged against the FP32 resolution of
+    # the optimum (gradient and value floors, tests/_fitcheck.py): the gradient's float atomics
+    # make its last digits, and so the stopping point, vary between runs
+    from tests._fitcheck import sampled_fit_check
+    worst, fl, vfl, unc, jt = sampled_fit_check(csx, case, res, list(range(wl.nconf * wl.nreal)))
+    print("worst |err|/tol %.3f; floors %d/%d; unconstrained %d; joint %d" % (worst, fl, vfl, unc, jt))
 
 
 # ------------------------------------------------------------------------------ AdaTopK -------
