@@ -191,13 +191,37 @@ def oracle_sample(inp, step: int = 0, pool=None):
     return {"value": n / wall, "unit": "fits/s", "cores": nsample, "kind": "oracle",
             "sample": "%d of %d problems: realization 0 of the configurations with P nearest the "
                       "scan's 10th percentile (%d; P %d..%d), nside 64, 32512 pixels, FP64 "
-                      "numpy/scipy L-BFGS-B plus Newton polish, one process per core; smaller P than "
+                      "numpy/scipy L-BFGS-B (no Newton polish), one process per core; smaller P than "
                       "the scan's median (%d), so the host rate is an upper bound for the full mix"
                       % (n, wl.nconf * wl.nreal, int(round(pq)), min(Ps), max(Ps),
                          int(np.median(wl.P))),
             "wall_s": wall,
             "single_fit_s_mean": float(np.mean([d[0] for d in done])),
             "oracle_iters_mean": float(np.mean([d[1] for d in done]))}
+
+
+def oracle_spectra_sample(inp, nprob: int = 10):
+    """The residual-spectra oracle (total, systematic and statistical pseudo-spectra to l = 150 on
+    the scan's cut sky) on one configuration's `nprob` realizations (seeded normal maps: the cost
+    does not depend on their values), in this process with numpy's BLAS threads."""
+    import numpy as np
+    from oracle import spectra as osp
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([int(i.get("num_threads", 1)) for i in threadpool_info()] or [1])
+    except Exception:
+        threads = 1
+    wl = inp["wl"]
+    rng = np.random.default_rng(0)
+    s_hat = rng.normal(size=(nprob, wl.npix, 2))
+    s_true = rng.normal(size=(wl.npix, 2))
+    r_sys = 0.1 * rng.normal(size=(nprob, wl.npix, 2))
+    t0 = time.time()
+    osp.residual_spectra(SCAN["nside"], wl.sky.pix, s_hat, s_true, r_sys, SPECTRA["lmax"])
+    wall = time.time() - t0
+    return {"value": nprob / wall, "unit": "problems/s", "cores": threads, "kind": "oracle",
+            "sample": "%d problems' residual maps (tot, syst, stat), nside 64 cut sky, l <= 150, "
+                      "FP64 direct sums over the pixels" % nprob, "wall_s": wall}
 
 
 # ----------------------------------------------------------------------------- CUDA arm -------
@@ -213,6 +237,8 @@ def run_csx(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     inp = make_inputs(rank, args.nconf)
     cpu_base = oracle_sample(inp) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if cpu_base is not None and not args.no_spectra:
+        cpu_base["residual_spectra"] = oracle_spectra_sample(inp)
 
     torch.cuda.set_device(local)
     dist = None
@@ -574,7 +600,17 @@ def kmeans_rates(csx, inp):
         for j in range(3):
             ref.setdefault(int(wl.K[c, j]), wl.labels[c, j])
     mismatched = sum(int(not np.array_equal(lab[i], ref[k])) for i, k in enumerate(ks))
+    # the host generator (the same Lloyd iterations in numpy, one process) on a bounded sample:
+    # the labelings of the largest K, where the work per labeling is largest
+    import time as _t
+    big = [k for k in ks if 1 < k < n][-2:]
+    h0 = _t.time()
+    for k in big:
+        km.spherical_kmeans(vec, k, 100 + k)
+    host_s = _t.time() - h0
     return {"labelings": len(ks), "pixels": n, "ms": ms, "labelings_per_s": len(ks) / (ms * 1e-3),
+            "host_generator": {"labelings": len(big), "K": big, "s": host_s,
+                               "labelings_per_s": len(big) / host_s, "processes": 1},
             "iters_mean": float(iters.float().mean()), "mismatched_vs_generator": mismatched,
             "timing": "CUDA events around one csx_kmeans launch (one CTA per labeling)"}
 
