@@ -259,7 +259,15 @@ def run_csx(args):
     model = csx.Model(wl.sky.nu)
     sky = csx.Sky(d, noise="separable", ninv_band=inp["nb32"], w=w)
     opts = dict(path=args.path, threads=args.threads)
-    path = "stream" if args.path == "stream" else "moment"  # auto picks moment (separable noise)
+    tuned = None
+    if args.path == "auto" and args.threads == 0:
+        # launch configuration of the fit picked by timing the candidates on a sample of the scan
+        # (untimed; re-tuned every run rather than read from a cache made by another build)
+        from paper_2604_08463_b300 import autotune
+        opts, entry = autotune.tune_fit(csx, model, sky, labels, K, beta0)
+        tuned = {"chosen": "%s/%d" % (opts["path"], opts["threads"]), "candidates_ms": entry["ms"],
+                 "sample": "the whole scan, every problem capped at 10 iterations"}
+    path = opts["path"] if opts["path"] != "auto" else "moment"  # auto: moment (separable noise)
     _, _, ncell_d = csx.build_cells(labels, K)
     ncell = ncell_d.cpu().numpy().astype(np.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -450,7 +458,9 @@ def run_csx(args):
         return
     launches_per_step = 4 + (1 if path == "moment" else 0)
     # DRAM traffic of one fit launch from the ncu capture (moment path only), scaled by units
-    traffic = TRAFFIC_FIT_PER_CELL_EVAL * unit_evals if path == "moment" else None
+    # the DRAM traffic per cell evaluation was captured with 128-thread CTAs
+    traffic = (TRAFFIC_FIT_PER_CELL_EVAL * unit_evals
+               if path == "moment" and opts["threads"] in (0, 128) else None)
     frac_mem, frac_alu = achieved / hbm, achieved_tf / fp32_peak
     if frac_alu >= frac_mem:
         roof = {"kernel": "k_fit (persistent fit)", "bound": "alu", "achieved": achieved_tf,
@@ -490,7 +500,8 @@ def run_csx(args):
                    "nreal": nreal, "problems_per_gpu": nprob, "mean_P": float(wl.P.mean()),
                    "max_P": int(wl.P.max()), "fit_path": path,
                    "l2": "256 MiB buffer written before every timed step (L2 is 126 MB)",
-                   "parallelism": "weak: each rank fits its own 1000 configurations"},
+                   "parallelism": "weak: each rank fits its own 1000 configurations",
+                   "fit_launch": tuned or dict(path=args.path, threads=args.threads)},
         "cluster_pixel_evals_per_s": float(nev.sum()) * npix / (fit_ms * 1e-3),
         "cell_evals_per_s": float((nev * ncell[conf_of]).sum()) / (fit_ms * 1e-3),
         "mean_cells": float(ncell.mean()),
