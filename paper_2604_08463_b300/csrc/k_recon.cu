@@ -5,6 +5,11 @@
 
 namespace csx {
 
+#ifndef CSX_RECON_PPT
+#define CSX_RECON_PPT 16  // pixels per thread of k_recon
+#endif
+constexpr int RECON_PPT = CSX_RECON_PPT;
+
 // Tables for every problem of a batch: problem q's rows start at row probs[q].toff.
 __global__ void k_recon_tables(Bands b, int nprob, const ProbDesc* __restrict__ probs,
                                const float* __restrict__ beta, float* __restrict__ tables,
@@ -46,7 +51,8 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
   float nb[NB];
 #pragma unroll
   for (int f = 0; f < NB; ++f) nb[f] = a.ninv_band[f];
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  // per-thread partial sums in FP32 (a thread takes a few pixels), FP64 across the warps
+  float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.npix; p += gridDim.x * blockDim.x) {
     const int kd = lab[p], kt = lab[a.npix + p], ks = lab[2 * a.npix + p];
     float sq[3] = {nan_f(), nan_f(), nan_f()}, su[3] = {nan_f(), nan_f(), nan_f()};
@@ -121,13 +127,13 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
       a.r_sys[pq * 2] = rq;
       a.r_sys[pq * 2 + 1] = ru;
     }
-    acc[0] += (double)rq * rq + (double)ru * ru;
-    acc[1] += (double)var;
-    acc[2] += (double)sq[0];
-    acc[3] += (double)sq[0] * sq[0];
-    acc[4] += (double)su[0];
-    acc[5] += (double)su[0] * su[0];
-    acc[6] += 1.0;
+    acc[0] = fmaf(rq, rq, fmaf(ru, ru, acc[0]));
+    acc[1] += var;
+    acc[2] += sq[0];
+    acc[3] = fmaf(sq[0], sq[0], acc[3]);
+    acc[4] += su[0];
+    acc[5] = fmaf(su[0], su[0], acc[5]);
+    acc[6] += 1.f;
   }
   if (a.metrics) {
 #pragma unroll
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) sred[k * 8 + w] = acc[k];
+      for (int k = 0; k < 7; ++k) sred[k * 8 + w] = (double)acc[k];
     }
     __syncthreads();
     if (threadIdx.x < 7) {
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(256) k_recon(ReconArgs a) {
 
 int launch_recon(const ReconArgs& a, cudaStream_t s) {
   if (a.nprob == 0) return CSX_OK;
-  int bx = (a.npix + 256 * 8 - 1) / (256 * 8);
+  int bx = (a.npix + 256 * RECON_PPT - 1) / (256 * RECON_PPT);
   if (bx < 1) bx = 1;
   for (int q0 = 0; q0 < a.nprob; q0 += 65535) {
     ReconArgs b = a;

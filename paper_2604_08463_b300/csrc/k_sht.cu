@@ -259,7 +259,6 @@ __device__ __forceinline__ void alm_stage(const AlmArgs& a, int b0, int nb, int 
 template <int MB, bool RESID>
 __global__ void __launch_bounds__(ALM_NT_MAX, CSX_ALM_MINB) k_alm_cl(const AlmArgs a) {
   static_assert(!RESID || MB % 2 == 0, "residual mode takes maps in pairs");
-  constexpr int NK = RESID ? 3 : 2;  // spectra per map (plain) or per pair (residual: X, Y, X - Y)
   extern __shared__ __align__(16) float4 alm_smem[];
   const int L1 = a.lmax + 1, nr = a.nring;
   float4* sd = alm_smem;                                      // [stages][2][MB][nring]
