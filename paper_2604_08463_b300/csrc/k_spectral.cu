@@ -103,11 +103,15 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 #ifndef CSX_TS_MINB
 #define CSX_TS_MINB (512 / CSX_TS_NT)
 #endif
+#ifndef CSX_TS_GRADVEC
+#define CSX_TS_GRADVEC 0  // 1: the gradient kernel also evaluates pixels from the run vectors
+#endif
 constexpr int TS_NT = CSX_TS_NT;                    // threads = pixels per tile
 constexpr int TS_NW = TS_NT / 32;
 constexpr int TS_S = CSX_TS_S;                      // pipeline stages
 constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
 constexpr int TS_RUNVEC = 32;  // runs per tile whose band vectors are kept in the run table
+constexpr bool TS_GRADVEC = CSX_TS_GRADVEC != 0;
 
 template <int NOISE>
 struct TsShape {
@@ -246,14 +250,14 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
         run_scalars<GRAD>(tab + (long long)t.x * NB, tab + (long long)(a.Kd + t.y) * NB,
                           tab + (long long)(a.Kd + a.KT + t.y) * NB,
                           tab + (long long)(a.Kd + 2 * a.KT + t.z) * NB, a.ninv_band, a.bands,
-                          n0, s_sc + 16 * r, (!GRAD && r < TS_RUNVEC) ? s_vec + 80 * r : nullptr);
+                          n0, s_sc + 16 * r, ((!GRAD || TS_GRADVEC) && r < TS_RUNVEC) ? s_vec + 80 * r : nullptr);
       }
       __syncthreads();
       if (valid) {
         float sc[NSC];
         load_scalars(s_sc + 16 * rid, sc);
         const float wpx = NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f;
-        if (!GRAD && rid < TS_RUNVEC)
+        if ((!GRAD || TS_GRADVEC) && rid < TS_RUNVEC)
           acc += cell_pixel_vec<GRAD>(dq, du, a.ninv_band, s_vec + 80 * rid, sc, wpx, g0, g1, g2);
         else
           acc += cell_pixel<GRAD>(dq, du, tab + (long long)kd * NB,
