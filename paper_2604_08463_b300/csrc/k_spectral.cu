@@ -71,8 +71,8 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 
 // ---------------------------------------------------------------------------------------------
 // Streaming likelihood (+ gradient) of Eqs. 3-4 and Sec. 3.3.1, TMA-staged. Grid (pixel blocks,
-// problems); a CTA takes tiles of TS_NT consecutive pixels of its problem, t = blockIdx.x,
-// blockIdx.x + gridDim.x, ... One thread keeps up to TS_S tiles of d (and of N^-1 for per-pixel
+// problems); a CTA takes a contiguous range of tiles of TS_NT consecutive pixels of its problem
+// (CSX_TS_CONTIG; else tiles strided by the grid). One thread keeps up to TS_S tiles of d (and of N^-1 for per-pixel
 // noise) in flight with bulk-tensor copies into a ring of shared-memory stages (128-byte swizzled
 // rows, so the per-pixel 16-byte reads are free of bank conflicts); every thread then reads its
 // pixel from shared memory. Labels and hit weights of the next tile are fetched into registers one
@@ -80,8 +80,10 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 //
 // Separable / homogeneous noise: the pixels of a tile are split into runs of consecutive pixels
 // with equal labels (within a warp); the Gram-Schmidt scalars of each run -- and, for L alone and
-// the first TS_RUNVEC runs of a tile, its band vectors -- are formed once, by one thread, into a
-// shared run table (run_scalars), and every pixel is then evaluated in its run's basis
+// the first TS_RUNVEC / (warps) runs of a warp, its band vectors -- are formed by the run's head
+// lane into its warp's part of the run table (run_scalars; CSX_TS_WARPRUNS, while the tile's data is
+// still in flight; else by one thread per run of the tile into a block-wide table behind two more
+// barriers), and every pixel is then evaluated in its run's basis
 // (cell_pixel_vec from the stored vectors; cell_pixel from the SED table rows otherwise: with the
 // gradient, the stored-vector form measured slower, its three extra vectors costing registers). Per-pixel noise: each pixel's own Gram-Schmidt solve (pixel_eval).
 //
@@ -103,6 +105,15 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 #ifndef CSX_TS_MINB
 #define CSX_TS_MINB (512 / CSX_TS_NT)
 #endif
+#ifndef CSX_TS_WARPRUNS
+#define CSX_TS_WARPRUNS 1  // 1: each warp forms the scalars of its own runs (no block-wide table)
+#endif
+#ifndef CSX_TS_CONTIG
+#define CSX_TS_CONTIG 1  // 1: each CTA streams a contiguous range of tiles (else tiles strided by the grid)
+#endif
+#ifndef CSX_TS_RUNCACHE
+#define CSX_TS_RUNCACHE 0  // 1: a warp keeps its runs' scalars across tiles (with CSX_TS_WARPRUNS)
+#endif
 #ifndef CSX_TS_GRADVEC
 #define CSX_TS_GRADVEC 0  // 1: the gradient kernel also evaluates pixels from the run vectors
 #endif
@@ -112,6 +123,10 @@ constexpr int TS_S = CSX_TS_S;                      // pipeline stages
 constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
 constexpr int TS_RUNVEC = 32;  // runs per tile whose band vectors are kept in the run table
 constexpr bool TS_GRADVEC = CSX_TS_GRADVEC != 0;
+constexpr bool TS_WARPRUNS = CSX_TS_WARPRUNS != 0;
+constexpr bool TS_CONTIG = CSX_TS_CONTIG != 0;
+constexpr bool TS_RUNCACHE = CSX_TS_RUNCACHE != 0;
+constexpr int TS_RUNVEC_W = TS_RUNVEC / (CSX_TS_NT / 32);  // run vectors per warp
 
 template <int NOISE>
 struct TsShape {
@@ -142,7 +157,11 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   float* sgrad = reinterpret_cast<float*>(stage0 + TS_S * Sh::SB + Sh::RB);
   const int q = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ntile = (a.npix + TS_NT - 1) / TS_NT;
-  const int my = ((int)blockIdx.x < ntile) ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // tiles of this CTA: tile(j) = t0 + j (a contiguous range) or blockIdx.x + j gridDim.x (strided)
+  const int t0 = TS_CONTIG ? (int)(((long long)blockIdx.x * ntile) / gridDim.x) : (int)blockIdx.x;
+  const int tstep = TS_CONTIG ? 1 : (int)gridDim.x;
+  const int my = TS_CONTIG ? (int)((((long long)blockIdx.x + 1) * ntile) / gridDim.x) - t0
+                           : (((int)blockIdx.x < ntile) ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   const float* tab = a.tables + (long long)q * a.rows * NB;
   float* ggl = GRAD ? a.grad + (long long)q * a.P : nullptr;
   float* gacc = SMEM_GRAD ? sgrad : ggl;
@@ -156,7 +175,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   __syncthreads();
   auto issue = [&](int j) {
     const int s = j % TS_S;
-    const int p0 = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT;
+    const int p0 = (t0 + j * tstep) * TS_NT;
     unsigned char* st = stage0 + s * Sh::SB;
     mbar_expect_tx(&full[s], Sh::SB);
     tma_load_3d(st, &md, 0, p0, q, &full[s]);
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   int nkd = 0, nkt = 0, nks = 0;
   float nw = 1.f;
   auto fetch = [&](int j) {
-    const int p = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT + tid;
+    const int p = (t0 + j * tstep) * TS_NT + tid;
     if (j < my && p < a.npix) {
       nkd = __ldg(ld + p);
       nkt = __ldg(lt + p);
@@ -186,8 +205,59 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   bool bad = false;
   int j = 0;
   bool timed_out = false;
+  constexpr bool WR = Sh::RUNS && TS_WARPRUNS;
+  int wnent = 0;  // entries of this warp's run cache
   for (; j < my; ++j) {
     const int s = j % TS_S;
+    // per-warp run table: the labels of this tile are already in registers, so the head lane of
+    // each run of equal labels in a warp forms the run's scalars while the tile's data is in flight
+    int wkd = nkd, wkt = nkt, wks = nks, wslot = 0;
+    bool wvalid = false;
+    if (WR) {
+      const int pw = (t0 + j * tstep) * TS_NT + tid;
+      wvalid = pw < a.npix && (unsigned)wkd < (unsigned)a.Kd && (unsigned)wkt < (unsigned)a.KT &&
+               (unsigned)wks < (unsigned)a.Ks;
+      const int pkd = __shfl_up_sync(0xffffffffu, wkd, 1), pkt = __shfl_up_sync(0xffffffffu, wkt, 1),
+                pks = __shfl_up_sync(0xffffffffu, wks, 1);
+      const bool pv = __shfl_up_sync(0xffffffffu, wvalid, 1);
+      const bool whead = wvalid && (lane == 0 || !pv || wkd != pkd || wkt != pkt || wks != pks);
+      const unsigned whb = __ballot_sync(0xffffffffu, whead);
+      __syncwarp();  // the warp's reads of the previous tile's table are done
+      bool miss = whead;
+      if (TS_RUNCACHE) {
+        // runs seen by this warp in earlier tiles keep their slot: look the label triple up
+        int found = -1;
+        for (int e = 0; e < wnent; ++e) {  // wnent is the same in every lane
+          const int4 t = s_trip[warp * 32 + e];
+          if (t.x == wkd && t.y == wkt && t.z == wks) found = e;
+        }
+        const unsigned mm = __ballot_sync(0xffffffffu, whead && found < 0);
+        if (wnent + __popc(mm) > 32) {  // table full: start it again with this tile's runs
+          wnent = 0;
+          found = -1;
+        }
+        miss = whead && found < 0;
+        const unsigned mb = __ballot_sync(0xffffffffu, miss);
+        wslot = miss ? wnent + __popc(mb & ((1u << lane) - 1u)) : found;
+        wnent += __popc(mb);
+      } else {
+        wslot = __popc(whb & ((2u << lane) - 1u)) - 1;
+      }
+      if (miss) {
+        if (TS_RUNCACHE) s_trip[warp * 32 + wslot] = make_int4(wkd, wkt, wks, 0);
+        run_scalars<GRAD>(tab + (long long)wkd * NB, tab + (long long)(a.Kd + wkt) * NB,
+                          tab + (long long)(a.Kd + a.KT + wkt) * NB,
+                          tab + (long long)(a.Kd + 2 * a.KT + wks) * NB, a.ninv_band, a.bands,
+                          n0, s_sc + 16 * (warp * 32 + wslot),
+                          ((!GRAD || TS_GRADVEC) && wslot < TS_RUNVEC_W)
+                              ? s_vec + 80 * (warp * TS_RUNVEC_W + wslot) : nullptr);
+      }
+      if (TS_RUNCACHE) {  // every pixel takes its run head's slot
+        const unsigned upto = whb & ((2u << lane) - 1u);
+        const int hl = upto ? 31 - __clz(upto) : lane;
+        wslot = __shfl_sync(0xffffffffu, wslot, hl);
+      }
+    }
     const bool ok = mbar_wait_bounded(&full[s], (unsigned)(j / TS_S) & 1u, TS_WAIT_CYCLES);
     const float4* row = reinterpret_cast<const float4*>(stage0 + s * Sh::SB);
     float dq[NB], du[NB], nn[NB];
@@ -209,7 +279,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
     int kd = nkd, kt = nkt, ks = nks;
     const float wp = nw;
     fetch(j + 1);
-    const int p = ((int)blockIdx.x + j * (int)gridDim.x) * TS_NT + tid;
+    const int p = (t0 + j * tstep) * TS_NT + tid;
     bool valid = p < a.npix;
     if (valid && ((unsigned)kd >= (unsigned)a.Kd || (unsigned)kt >= (unsigned)a.KT ||
                   (unsigned)ks >= (unsigned)a.Ks)) {
@@ -220,7 +290,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
     // pixel or where a label changes
     bool head = false;
     unsigned hb = 0u;
-    if (Sh::RUNS) {
+    if (Sh::RUNS && !WR) {
       const int pkd = __shfl_up_sync(0xffffffffu, kd, 1), pkt = __shfl_up_sync(0xffffffffu, kt, 1),
                 pks = __shfl_up_sync(0xffffffffu, ks, 1);
       const bool pv = __shfl_up_sync(0xffffffffu, valid, 1);
@@ -234,7 +304,22 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
     }
     if (tid == 0 && j + TS_S < my) issue(j + TS_S);
     float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (Sh::RUNS) {
+    if (WR) {
+      if (valid) {  // the block barrier above published the warp's run table
+        float sc[NSC];
+        load_scalars(s_sc + 16 * (warp * 32 + wslot), sc);
+        const float wpx = NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f;
+        if ((!GRAD || TS_GRADVEC) && wslot < TS_RUNVEC_W)
+          acc += cell_pixel_vec<GRAD>(dq, du, a.ninv_band, s_vec + 80 * (warp * TS_RUNVEC_W + wslot),
+                                      sc, wpx, g0, g1, g2);
+        else
+          acc += cell_pixel<GRAD>(dq, du, tab + (long long)kd * NB,
+                                  tab + (long long)(a.Kd + kt) * NB,
+                                  tab + (long long)(a.Kd + a.KT + kt) * NB,
+                                  tab + (long long)(a.Kd + 2 * a.KT + ks) * NB, a.ninv_band,
+                                  a.bands, sc, wpx, g0, g1, g2);
+      }
+    } else if (Sh::RUNS) {
       int roff = 0, nruns = 0;
 #pragma unroll
       for (int w = 0; w < TS_NW; ++w) {
