@@ -37,6 +37,9 @@ namespace csx {
 #ifndef CSX_DFT_MC
 #define CSX_DFT_MC 8      // maps per k_ring_dft block
 #endif
+#ifndef CSX_DFT_SINCOS
+#define CSX_DFT_SINCOS 0  // 1: twiddles re-anchored by sincospif (else from the shared table; measured faster)
+#endif
 #ifndef CSX_ALM_UNROLL
 #define CSX_ALM_UNROLL 4  // ring-loop unroll of k_alm_cl
 #endif
@@ -184,7 +187,14 @@ __global__ void __launch_bounds__(DFT_NT_MAX) k_ring_dft(const DftArgs a) {
       if (j == jprev + 1 && (i % DFT_REANCHOR) != 0) {
         w = make_float2(w.x * step.x - w.y * step.y, w.x * step.y + w.y * step.x);
       } else {
-        w = tw[(mm * j) % n];  // mm, j < n <= 4 SHT_MAX_NSIDE: the product fits in int
+        const int k = (mm * j) % n;  // mm, j < n <= 4 SHT_MAX_NSIDE: the product fits in int
+        if (CSX_DFT_SINCOS) {  // computed: table reads at k = m j mod n collide across a warp's m
+          float sn, cs;
+          sincospif(2.f * (float)k / (float)n, &sn, &cs);
+          w = make_float2(cs, -sn);
+        } else {
+          w = tw[k];
+        }
       }
       jprev = j;
       const float4* v4 = reinterpret_cast<const float4*>(val + i * DFT_MC);  // two maps a load
