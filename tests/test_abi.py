@@ -124,3 +124,10 @@ def test_spectra_arguments_are_refused_on_the_host(lib):
                            ctypes.c_void_p(0x10000), None)
     assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
     assert lib.csx_sht_plan_destroy(None) == 0
+
+
+def test_residual_spectra_arguments_are_refused_on_the_host(lib):
+    import ctypes
+    ok = ctypes.c_void_p(0x10000)
+    rc = lib.csx_residual_cl(None, 2, ok, 12, 6, 3, None, ok, 1, ok, ok, ok, None)
+    assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
