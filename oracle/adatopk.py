@@ -35,6 +35,13 @@ Readings where App. A is silent or garbled (the CUDA path applies the same ones)
   - the direction is also zeroed where a free parameter sits on a bound and d points out of the box
     (a just-released parameter whose AdaBelief momentum still points outward would otherwise make
     the step limit zero for every parameter); eta is kept after a zero-length step.
+
+Parity pins (tests/test_oracle_adatopk.py): the Top-K release rule on hand-made pivots and scores
+(K = 0 frees the single highest, K = 1 all, ties to the lowest index); a separable box quadratic
+reaches clip(c, 0, 1) (the closed-form minimiser, two coordinates on bounds); a start with every
+coordinate on a bound is released where the gradient points inward; rescaling the objective by
+1e20 leaves the minimiser unchanged; on the plain nside-8 sky the fit lands on scipy's L-BFGS-B
+optimum (a library routine) within the parity tolerances.
 """
 from __future__ import annotations
 
