@@ -57,7 +57,10 @@ constexpr int DFT_NT_MAX = 256;  // threads of k_ring_dft: one m per thread, lma
 constexpr int DFT_MC = CSX_DFT_MC;  // maps per k_ring_dft block (accumulators in registers)
 constexpr int kAlmUnroll = CSX_ALM_UNROLL;
 constexpr int kAlmStages = CSX_ALM_STAGES;
-constexpr int DFT_REANCHOR = 16;  // twiddles advanced by complex products at most this many pixels
+#ifndef CSX_DFT_REANCHOR
+#define CSX_DFT_REANCHOR 16
+#endif
+constexpr int DFT_REANCHOR = CSX_DFT_REANCHOR;  // twiddles advanced by complex products at most this many pixels
 constexpr int ALM_NT_MAX = 512;  // threads of k_alm_cl: one (l, m) pair of an m group each
 constexpr size_t ALM_SMEM_MAX = 200 << 10;  // staged ring coefficients + spectra per block
 constexpr int SHT_MAX_NSIDE = 256;
