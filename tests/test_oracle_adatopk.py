@@ -70,3 +70,28 @@ def test_plain_likelihood_matches_the_library_optimum():
     assert info["status"] == 0
     assert np.all(np.abs(x - xr) <= 0.5 * np.array([1e-3, 1e-2, 1e-3])), (x, xr)
     assert L >= Lr - 1e-9 * abs(Lr) and L - Lr <= 1e-6 * abs(Lr)
+
+
+def test_adabelief_two_steps_by_hand():
+    """AdaBelief (Zhuang et al. 2020) with bias correction, worked by hand for two steps of a
+    two-component gradient, beta1 = 0.9, beta2 = 0.999 (eps = 1e-16 is far below these digits):
+      component A, g = 1 then 3:
+        m1 = 0.1, s1 = 0.001 (1 - 0.1)^2 = 8.1e-4; m_hat = 1, s_hat = 0.81  ->  d1 = -1 / 0.9 = -10/9
+        m2 = 0.09 + 0.3 = 0.39, s2 = 0.999 * 8.1e-4 + 0.001 (3 - 0.39)^2 = 7.62129e-3;
+        m_hat = 0.39 / 0.19 = 39/19, s_hat = 7.62129e-3 / 1.999e-3  ->  d2 = -(39/19) / sqrt(762129/199900)
+      component B, g = -2 then 0:
+        m1 = -0.2, s1 = 0.001 (1.8)^2 = 3.24e-3  ->  d1 = 2 / 1.8 = 10/9
+        m2 = -0.18, s2 = 0.999 * 3.24e-3 + 0.001 (0.18)^2 = 3.26916e-3  ->  d2 = (18/19) / sqrt(326916/199900)
+    Adam's g^2 in place of (g - m)^2 gives -1 and -0.918 for component A, and dropping the bias
+    correction gives d1 = -0.1 / sqrt(8.1e-4) = -3.51: both fail here."""
+    m = np.zeros(2)
+    s = np.zeros(2)
+    d1, m, s = at.adabelief(np.array([1.0, -2.0]), m, s, 1)
+    np.testing.assert_allclose(d1, [-10.0 / 9.0, 10.0 / 9.0], rtol=1e-12)
+    np.testing.assert_allclose(m, [0.1, -0.2], rtol=1e-12)
+    np.testing.assert_allclose(s, [8.1e-4, 3.24e-3], rtol=1e-12)
+    d2, m, s = at.adabelief(np.array([3.0, 0.0]), m, s, 2)
+    np.testing.assert_allclose(m, [0.39, -0.18], rtol=1e-12)
+    np.testing.assert_allclose(s, [7.62129e-3, 3.26916e-3], rtol=1e-12)
+    np.testing.assert_allclose(d2, [-(39.0 / 19.0) / np.sqrt(762129.0 / 199900.0),
+                                    (18.0 / 19.0) / np.sqrt(326916.0 / 199900.0)], rtol=1e-12)
