@@ -127,6 +127,38 @@ def gauss_newton_diagonal(nu, d, ninv, labels, K, beta):
     ])
 
 
+def gauss_newton_hessian(nu, d, ninv, labels, K, beta):
+    """The Gauss-Newton Hessian [P, P] of chi2_min(beta) with the amplitudes profiled out (variable
+    projection): H = 2 sum_p sum_s J^T N J, J[:, theta] = P_perp (dA/dtheta) s_hat, where
+    P_perp = I - A M^-1 A^T N projects onto the N-orthogonal complement of the columns of A. Per
+    pixel, with delta_theta the derivative column of theta (dust for beta_d and T_d, synchrotron for
+    beta_s) and j(theta) the column it enters:
+      H_p[theta, phi] = 2 (delta_theta^T N P_perp delta_phi) sum_s s_hat_j(theta) s_hat_j(phi),
+    added at the pixel's own patch parameters. It is the Hessian itself where the residual
+    d - A s_hat vanishes (the terms it drops are proportional to the residual)."""
+    kd, kt, ks = (int(k) for k in K)
+    bd, td, bs = pixel_parameters(beta, labels, K)
+    A = mixing_matrix(nu, bd, td, bs)
+    dbd, dtd, dbs = mixing_derivatives(nu, bd, td, bs)
+    M, b = normal_equations(A, ninv, d)
+    s = np.linalg.solve(M[:, None, :, :], b[..., None])[..., 0]
+    delta = np.stack([dbd, dtd, dbs], axis=2)                       # [npix, F, 3]
+    nd = ninv[:, :, None] * delta
+    G = np.einsum("pfi,pfj->pij", delta, nd)                        # delta^T N delta
+    AtNd = np.einsum("pfk,pfi->pki", A, nd)                          # A^T N delta  [npix, 3, 3]
+    G = G - np.einsum("pki,pkl,plj->pij", AtNd, np.linalg.inv(M), AtNd)
+    col = np.array([1, 1, 2])
+    W = np.einsum("psi,psj->pij", s[:, :, col], s[:, :, col])       # sum_s s_j(theta) s_j(phi)
+    Hp = 2.0 * G * W
+    idx = np.stack([labels[0], kd + labels[1], kd + kt + labels[2]], axis=1)  # [npix, 3]
+    P = kd + kt + ks
+    H = np.zeros((P, P))
+    for i in range(3):
+        for j in range(3):
+            np.add.at(H, (idx[:, i], idx[:, j]), Hp[:, i, j])
+    return H
+
+
 def gradient_term_scale(nu, d, ninv, labels, K, beta, data_scale=False):
     """S_theta = 2 sum over the pixels of theta's patch, the Stokes parameters and the bands of
     |w_r (dA/dtheta) s_hat| : the summed magnitude of the terms whose signed sum is dL/dtheta.

@@ -5,8 +5,9 @@ Columns, for band centre nu:
   dust: A_d(nu) = nu / (exp(h nu / k T_d) - 1) * (exp(h nu0 / k T_d) - 1) / nu0 * (nu / nu0)^beta_d
   sync: A_s(nu) = (nu / nu0)^beta_s
 with nu0 = 353 GHz (dust) and 23 GHz (synchrotron). Eq. 5 is a ratio of Rayleigh-Jeans
-brightnesses; the maps are in K_CMB, so each foreground column is multiplied by g(nu) / g(nu0),
-g(nu) = (e^x - 1)^2 / (x^2 e^x), x = h nu / (k T_CMB) (reading recorded in the design notes).
+brightnesses while the maps are in K_CMB (thermodynamic units), so each foreground column is read as
+multiplied by the Rayleigh-Jeans-to-K_CMB factor ratio g(nu) / g(nu0), g(nu) = (e^x - 1)^2 / (x^2 e^x),
+x = h nu / (k T_CMB); the beta derivatives are unaffected by it.
 
 Derivatives (closed form):
   dA_d/dbeta_d = A_d ln(nu/nu0),  dA_s/dbeta_s = A_s ln(nu/nu0),

@@ -339,3 +339,63 @@ def test_selection_argmin_and_ties():
     v, best = rc.total_residual_variance([[m(2.0, 1.0)], [m(0.0, 1.0)], [m(0.0, 1.0)]], npix=1)
     np.testing.assert_allclose(v, [2.0, 1.0, 1.0])
     assert best == 1
+
+
+def test_gauss_newton_diagonal_is_the_exact_curvature_at_a_noiseless_truth():
+    """With noise-free data d = A(beta_true) s and the amplitudes held at s, the residual vanishes at
+    beta_true, so the second derivative of f(beta) = sum_p sum_s (d - A(beta) s)^T N^-1 (d - A(beta) s)
+    there is exactly 2 sum (dA/dtheta s)^T N^-1 (dA/dtheta s): the Gauss-Newton diagonal. f is
+    formed here from the mixing matrix alone and differenced twice (central, O(h^2))."""
+    sk = S.make_sky(4, truth="uniform", hitcount=True)
+    rng = np.random.default_rng(5)
+    K = np.array([3, 2, 2])
+    labels = np.stack([rng.integers(0, K[j], sk.npix) for j in range(3)]).astype(np.int64)
+    for j in range(3):
+        labels[j, :K[j]] = np.arange(K[j])
+    beta = np.concatenate([np.full(K[0], 1.54), np.full(K[1], 20.0), np.full(K[2], -3.0)])
+    d = sk.data(None)
+    ninv = sk.ninv_pixel()
+    s = lk.gls_components(lk.pixel_mixing(NU, beta, labels, K), ninv, d)  # = the true amplitudes
+
+    def f(b):
+        r = d - np.einsum("pfi,psi->psf", lk.pixel_mixing(NU, b, labels, K), s)
+        return float(np.sum(r * ninv[:, None, :] * r))
+
+    assert f(beta) < 1e-20 * lk.data_norm(d, ninv)
+    H = lk.gauss_newton_diagonal(NU, d, ninv, labels, K, beta)
+    fd = np.empty_like(H)
+    for i in range(K.sum()):
+        h = 1e-3 if K[0] <= i < K[0] + K[1] else 1e-4
+        e = np.zeros(K.sum())
+        e[i] = h
+        fd[i] = (f(beta + e) - 2.0 * f(beta) + f(beta - e)) / h ** 2
+    np.testing.assert_allclose(H, fd, rtol=1e-5)
+
+
+def test_gauss_newton_hessian_is_the_exact_hessian_at_a_noiseless_truth():
+    """Where the residual vanishes (noise-free data at the true parameters) the Hessian of the
+    profiled chi2_min(beta) is exactly the Gauss-Newton form 2 J^T N J: compared with central
+    differences of the analytic gradient (itself pinned against differences of chi2_min). The
+    off-diagonal blocks couple the parameters of patches that share pixels."""
+    sk = S.make_sky(4, truth="uniform", hitcount=True)
+    rng = np.random.default_rng(6)
+    K = np.array([3, 2, 2])
+    labels = np.stack([rng.integers(0, K[j], sk.npix) for j in range(3)]).astype(np.int64)
+    for j in range(3):
+        labels[j, :K[j]] = np.arange(K[j])
+    beta = np.concatenate([np.full(K[0], 1.54), np.full(K[1], 20.0), np.full(K[2], -3.0)])
+    d = sk.data(None)
+    ninv = sk.ninv_pixel()
+    H = lk.gauss_newton_hessian(NU, d, ninv, labels, K, beta)
+    P = K.sum()
+    fd = np.empty((P, P))
+    for i in range(P):
+        h = 1e-4 if K[0] <= i < K[0] + K[1] else 1e-5
+        e = np.zeros(P)
+        e[i] = h
+        fd[:, i] = (lk.spectral_gradient(NU, d, ninv, labels, K, beta + e)[1] -
+                    lk.spectral_gradient(NU, d, ninv, labels, K, beta - e)[1]) / (2 * h)
+    np.testing.assert_allclose(H, 0.5 * (fd + fd.T), rtol=2e-5, atol=2e-6 * np.abs(H).max())
+    assert np.allclose(H, H.T) and np.linalg.eigvalsh(H).min() > 0
+    # its diagonal lies below the plain (unprojected) Gauss-Newton diagonal
+    assert np.all(np.diag(H) <= lk.gauss_newton_diagonal(NU, d, ninv, labels, K, beta) * (1 + 1e-12))
