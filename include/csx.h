@@ -26,7 +26,7 @@
  *     double). A misaligned pointer is refused with CSX_EINVAL before anything is enqueued.
  *   - Patch labels: int32 [3][npix] per configuration (beta_d, T_d, beta_s labelings), values in
  *     [0, K_j). Labels out of range make the affected problem's likelihood NaN (spectral calls,
- *     reconstruction) or the fit call return CSX_ELABEL.
+ *     reconstruction) or its fit status CSX_FIT_BADLABEL / CSX_FIT_NONPHYSICAL with L NaN (fit).
  *   - Parameters of one problem are packed [beta_d (K_d) | T_d (K_T) | beta_s (K_s)], P = sum K_j.
  */
 #ifndef CSX_H
@@ -40,13 +40,14 @@ extern "C" {
 
 #define CSX_MAX_BANDS 16
 #define CSX_NMETRIC 8
+#define CSX_MAX_K (1 << 24) /* largest patch count per parameter (larger K_j: CSX_EINVAL) */
 
 /* return codes */
 #define CSX_OK 0
 #define CSX_EINVAL (-1)   /* null or misaligned pointer, bad size or option */
 #define CSX_ECUDA (-2)    /* a CUDA runtime call failed */
 #define CSX_ENOMEM (-3)   /* scratch allocation failed */
-#define CSX_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define CSX_ETIMEOUT (-4) /* a bounded device wait gave up (reported by csx_device_status) */
 #define CSX_ELABEL (-5)   /* a label outside [0, K_j) was found */
 
 /* noise models: N_p^-1 = diag(ninv_band) | w_p diag(ninv_band) | diag(ninv_pix[p]) */
@@ -59,6 +60,7 @@ extern "C" {
 #define CSX_FIT_MAXITER 1
 #define CSX_FIT_NONPHYSICAL 2   /* non-finite likelihood at the start (e.g. singular A^T N^-1 A) */
 #define CSX_FIT_LINESEARCH 3    /* no acceptable step from the current point */
+#define CSX_FIT_BADLABEL 4      /* the configuration has a label outside [0, K_j) (moment path) */
 
 /* optimiser of csx_fit_batch: L-BFGS in Gauss-Newton-scaled variables, or AdaTopK (App. A:
  * AdaBelief directions, Top-K release of bound constraints, dynamic rescaling, backtracking) */
@@ -136,6 +138,14 @@ const char* csx_last_error(void);
 /* Free the scratch buffers of the current device. Synchronises the device. */
 int csx_release(void);
 
+/*
+ * Device-side failures found since the last call on the current device: synchronises `stream`,
+ * then returns CSX_ETIMEOUT if any bounded wait of a streaming-kernel launch gave up (a tensor
+ * copy that did not arrive within about 2 s; that problem's L was set to NaN and the kernel
+ * returned), CSX_ECUDA if the synchronisation failed, else CSX_OK. The record is cleared.
+ */
+int csx_device_status(void* stream);
+
 /* Fill `o` with the defaults listed in csx_fit_opts. */
 int csx_fit_defaults(csx_fit_opts* o);
 
@@ -173,6 +183,18 @@ int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* lab
                       float* grad, void* stream);
 
 /*
+ * The likelihood and adjoint gradient of csx_spectral_grad with every operation in FP64 (the data
+ * are read as stored, float32, and widened; SED tables, normal equations, Cholesky solve, residuals
+ * and sums in double): an on-device check of the FP32 kernels' rounding (the differentiation check
+ * at nside 128). B300's FP64 rate is a small fraction of its FP32 rate; this is not a fast path.
+ *   beta  device double [nprob][P];  L device double [nprob];  grad device double [nprob][P] or NULL
+ * Other arguments, layouts and errors as csx_spectral_grad.
+ */
+int csx_spectral_grad_f64(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                          const int32_t K[3], int32_t nprob, const double* beta, double* L,
+                          double* grad, void* stream);
+
+/*
  * csx_spectral_grad without any device allocation. The paper has no counterpart: this is an
  * interface for callers that cannot let a library call cudaMalloc -- applications whose device
  * memory belongs to their own pool allocator (an allocation behind its back can fail or fragment
@@ -181,14 +203,34 @@ int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* lab
  * scratch, the SED tables, lives in a static device array of 2^20 floats (4 MiB) that stays
  * resident on every device that loads the library until the process exits;
  * nprob x (K_d + 2 K_T + K_s) x 16 must not exceed 2^20, otherwise the call returns CSX_EINVAL and
- * enqueues nothing. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture begins. All calls on a
- * device share the array and it keeps the last call's contents: calls whose work overlaps on the
- * GPU (for example on different streams) race and must be serialised by the caller.
+ * enqueues nothing. The array's device address is looked up (cudaGetSymbolAddress) on the first
+ * call on a device and again on each later call made while `stream` is not capturing (so a
+ * re-created context gets its own address); make the first call on a device before any stream
+ * capture begins. All calls on a device share the array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (for example on different streams) race and must be
+ * serialised by the caller. K_j above CSX_MAX_K are refused like the other argument errors.
  */
 int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky, const int32_t* labels,
                               const int32_t K[3], int32_t nprob, const float* beta, double* L,
                               float* grad, void* stream);
+
+/*
+ * L and dL/dbeta by the cell-moment evaluation that csx_fit_batch uses for homogeneous or separable
+ * noise (Eq. 4 and Sec. 3.3.1 over the cells of equal (l_d, l_T, l_s), Sec. 2.2): for problem i
+ * (realization i, nprob <= sky->nreal), the residual moments of each cell are formed about the
+ * reference point beta_ref[i] (one pass over the pixels), then L = chi2_min - sum d^T N^-1 d and
+ * the gradient are evaluated at beta[i] from the moments alone. Same values as csx_spectral_grad
+ * up to FP32 rounding, which grows with |beta - beta_ref| (the moments are residuals about the
+ * reference point).
+ *   labels device int32 [3][npix];  K host int32[3]
+ *   beta_ref, beta  device float [nprob][P]
+ *   L      device double [nprob]; grad device float [nprob][P]  (overwritten; NaN for a
+ *          configuration with a label outside [0, K_j))
+ * Errors: CSX_EINVAL for per-pixel noise, NULL or misaligned pointers, bad sizes.
+ */
+int csx_cell_like_grad(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                       const int32_t K[3], int32_t nprob, const float* beta_ref, const float* beta,
+                       double* L, float* grad, void* stream);
 
 /*
  * Cells of each configuration: pixels sorted stably by (l_d, l_T, l_s) (Sec. 2.2-2.3).
@@ -211,8 +253,14 @@ int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const in
  *   nevals  device int32 [nconf * nreal] or NULL: likelihood evaluations performed per problem
  *           (each forward evaluation of a finite-difference gradient counts once)
  * Optimiser: L-BFGS in Gauss-Newton-scaled variables with the active-set bound handling and
- * step limit of App. A, line search on approximate Wolfe conditions. With the moment path the call
- * synchronises `stream` once (to read the cell counts).
+ * step limit of App. A, line search on approximate Wolfe conditions. The call does not
+ * synchronise: sizes come from K alone (the moment path's per-CTA scratch from the bound
+ * ncell <= min(npix, K_d K_T K_s) of each configuration), the problem descriptors and the
+ * longest-first work queue are formed on the device (on the host, from the bound, above 16384
+ * configurations). The result is deterministic: the same inputs give the same bits on every call
+ * (gradient sums are formed in a fixed order, not with floating-point atomics).
+ * A configuration with a label outside [0, K_j) gives its problems status CSX_FIT_BADLABEL (moment
+ * path) or CSX_FIT_NONPHYSICAL (streaming path) and L NaN.
  */
 int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
                   const int32_t* K, const csx_fit_opts* opts, const float* beta0, float* beta_out,

@@ -149,8 +149,29 @@ Bands make_bands(const csx_model& m) {
   return b;
 }
 
+Bands64 make_bands64(const csx_model& m) {
+  Bands64 b;
+  std::memset(&b, 0, sizeof(b));
+  const double h_over_k = 6.62607015e-34 / 1.380649e-23 * 1e9;
+  b.nf = m.nfreq;
+  b.xk0 = h_over_k * m.nu0_dust_ghz;
+  const bool kcmb = (m.units == 0);
+  const double ud = kcmb ? rj_to_kcmb(m.nu0_dust_ghz, m.t_cmb) : 1.0;
+  const double us = kcmb ? rj_to_kcmb(m.nu0_sync_ghz, m.t_cmb) : 1.0;
+  for (int f = 0; f < m.nfreq; ++f) {
+    const double nu = m.nu_ghz[f];
+    const double u = kcmb ? rj_to_kcmb(nu, m.t_cmb) : 1.0;
+    b.lnd[f] = std::log(nu / m.nu0_dust_ghz);
+    b.lns[f] = std::log(nu / m.nu0_sync_ghz);
+    b.xk[f] = h_over_k * nu;
+    b.cd[f] = nu / m.nu0_dust_ghz * u / ud;
+    b.cs[f] = u / us;
+  }
+  return b;
+}
+
 // ------------------------------------------------------------------------------ checks ---------
-static int check_model(const csx_model* m) {
+int check_model(const csx_model* m) {
   if (!m) return fail(CSX_EINVAL, "model is NULL");
   if (m->nfreq < 1 || m->nfreq > 15) return fail(CSX_EINVAL, "nfreq must be in 1..15");
   if (m->units != 0 && m->units != 1) return fail(CSX_EINVAL, "units must be 0 (K_CMB) or 1 (RJ)");
@@ -174,7 +195,7 @@ int check_align(const void* p, size_t align, const char* what) {
     if (rc_) return rc_;                                   \
   } while (0)
 
-static int check_sky(const csx_sky* s, int nfreq) {
+int check_sky(const csx_sky* s, int nfreq) {
   if (!s) return fail(CSX_EINVAL, "sky is NULL");
   // pixel rows are read as 16-byte vectors (and staged by tensor copies): 16-byte alignment
   int rc;
@@ -196,9 +217,10 @@ static int check_sky(const csx_sky* s, int nfreq) {
   return CSX_OK;
 }
 
-static int check_K(const int32_t* K) {
+int check_K(const int32_t* K) {
   for (int j = 0; j < 3; ++j)
-    if (K[j] < 1) return fail(CSX_EINVAL, "every K_j must be >= 1");
+    if (K[j] < 1 || K[j] > CSX_MAX_K)
+      return fail(CSX_EINVAL, "every K_j must be in [1, " + std::to_string(CSX_MAX_K) + "]");
   return CSX_OK;
 }
 
@@ -219,6 +241,15 @@ const char* csx_last_error(void) { return g_err.c_str(); }
 int csx_release(void) {
   CSX_CUDA(cudaDeviceSynchronize());
   scratch_release_all();
+  return CSX_OK;
+}
+
+int csx_device_status(void* stream) {
+  unsigned n = 0;
+  int rc = device_timeouts((cudaStream_t)stream, &n);
+  if (rc) return rc;
+  if (n) return fail(CSX_ETIMEOUT, std::to_string(n) + " bounded device wait(s) gave up since the "
+                                   "last check (the affected problems' L is NaN)");
   return CSX_OK;
 }
 
@@ -321,6 +352,52 @@ int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* lab
   return spectral_common(m, sky, labels, K, nprob, beta, L, grad, true, stream);
 }
 
+int csx_spectral_grad_f64(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                          const int32_t K[3], int32_t nprob, const double* beta, double* L,
+                          double* grad, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (!K) return fail(CSX_EINVAL, "K is NULL");
+  if ((rc = check_K(K))) return rc;
+  if (nprob < 0 || nprob > sky->nreal) return fail(CSX_EINVAL, "nprob must be in [0, sky->nreal]");
+  if (nprob == 0) return CSX_OK;
+  if (!beta || !L) return fail(CSX_EINVAL, "beta and L must not be NULL");
+  if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(beta, 8);
+  CSX_ALIGN(L, 8);
+  CSX_ALIGN(grad, 8);
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long P = (long long)K[0] + K[1] + K[2];
+  const long long rows = (long long)K[0] + 2LL * K[1] + K[2];
+  double* tables = (double*)scratch(SCR_TABLES, (size_t)nprob * rows * NB * sizeof(double), &rc);
+  if (rc) return rc;
+  CSX_CUDA(cudaMemsetAsync(L, 0, (size_t)nprob * sizeof(double), s));
+  if (grad) CSX_CUDA(cudaMemsetAsync(grad, 0, (size_t)nprob * P * sizeof(double), s));
+  Spec64Args a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = make_bands64(*m);
+  a.npix = sky->npix;
+  a.nprob = nprob;
+  a.Kd = K[0];
+  a.KT = K[1];
+  a.Ks = K[2];
+  a.P = (int)P;
+  a.rows = (int)rows;
+  a.noise_kind = sky->noise_kind;
+  a.d = sky->d;
+  a.w = sky->w;
+  a.ninv_pix = sky->ninv_pix;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.labels = labels;
+  a.beta = beta;
+  a.tables = tables;
+  a.L = L;
+  a.grad = grad;
+  return launch_spectral64(a, grad != nullptr, s);
+}
+
 int csx_build_cells(int32_t npix, int32_t nconf, const int32_t* labels, const int32_t* K,
                     int32_t* perm, int32_t* cell_off, int32_t* ncell, void* stream) {
   if (npix < 0 || nconf < 0) return fail(CSX_EINVAL, "npix and nconf must be >= 0");
@@ -391,74 +468,57 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   cudaStream_t s = (cudaStream_t)stream;
   const int npix = sky->npix;
 
-  // problem descriptors
-  std::vector<long long> coff(nconf + 1, 0);
-  int Pmax = 0, rows_max = 0;
+  // Sizes from the host-known K only: nothing is read back from the device, so the call returns
+  // once its work is enqueued. Problem descriptors and the longest-first queue order are formed on
+  // the device; the per-slot moment scratch is sized from the bound ncell <= min(npix, K_d K_T K_s).
+  int Pmax = 0, rows_max = 0, ncell_max = 0;
+  std::vector<long long> cost((size_t)nconf);
   for (int c = 0; c < nconf; ++c) {
     if ((rc = check_K(K + 3 * c))) return rc;
-    const int P = K[3 * c] + K[3 * c + 1] + K[3 * c + 2];
-    coff[c + 1] = coff[c] + P;
-    Pmax = std::max(Pmax, P);
-    rows_max = std::max(rows_max, K[3 * c] + 2 * K[3 * c + 1] + K[3 * c + 2]);
+    const long long kd = K[3 * c], kt = K[3 * c + 1], ks = K[3 * c + 2];
+    Pmax = std::max(Pmax, (int)(kd + kt + ks));
+    rows_max = std::max(rows_max, (int)(kd + 2 * kt + ks));
+    const long long bound = std::min<long long>((long long)npix, kd * kt * ks);
+    if (path == CSX_PATH_MOMENT) ncell_max = std::max(ncell_max, (int)bound);
+    cost[(size_t)c] = (path == CSX_PATH_MOMENT ? bound : 0) + 8 * (kd + kt + ks);
   }
   Pmax = (Pmax + 3) & ~3;
-  std::vector<ProbDesc> probs((size_t)nprob);
-  for (int c = 0; c < nconf; ++c)
-    for (int n = 0; n < sky->nreal; ++n) {
-      ProbDesc& d = probs[(size_t)c * sky->nreal + n];
-      d.conf = c;
-      d.real = n;
-      d.Kd = K[3 * c];
-      d.KT = K[3 * c + 1];
-      d.Ks = K[3 * c + 2];
-      d.P = d.Kd + d.KT + d.Ks;
-      d.poff = (long long)sky->nreal * coff[c] + (long long)n * d.P;
-      d.toff = 0;
-    }
-
-  // cells (moment path): built on the device, counts read back to size the per-slot scratch
-  int ncell_max = 0;
-  int *perm = nullptr, *coffs = nullptr, *ncell = nullptr;
-  std::vector<int> ncell_h(nconf, 0);
-  if (path == CSX_PATH_MOMENT) {
-    const size_t per = (size_t)npix;
-    char* cb = (char*)scratch(SCR_CELLS, (size_t)nconf * (2 * per + 1) * sizeof(int) + (size_t)nconf * 4 * sizeof(int) + 256, &rc);
-    if (rc) return rc;
-    perm = (int*)cb;
-    coffs = perm + (size_t)nconf * per;
-    ncell = coffs + (size_t)nconf * (per + 1);
-    int* Kdev = ncell + nconf;
-    {
-      TraceSpan tr("fit: cells", s);
-      CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
-      if ((rc = launch_cells(npix, nconf, labels, Kdev, perm, coffs, ncell, s))) return rc;
-      CSX_CUDA(cudaMemcpyAsync(ncell_h.data(), ncell, (size_t)nconf * sizeof(int), cudaMemcpyDeviceToHost, s));
-      CSX_CUDA(cudaStreamSynchronize(s));
-    }
-    for (int c = 0; c < nconf; ++c) {
-      if (ncell_h[c] < 0) return fail(CSX_ELABEL, "configuration " + std::to_string(c) + " has a label outside [0, K_j)");
-      ncell_max = std::max(ncell_max, ncell_h[c]);
-    }
-  }
-
-  TraceSpan trh("fit: host prep + copies", s);
-  // largest-first queue order (longest processing time first)
-  std::vector<int> order((size_t)nprob);
-  std::iota(order.begin(), order.end(), 0);
-  std::vector<double> cost((size_t)nprob);
-  for (long long q = 0; q < nprob; ++q) {
-    const ProbDesc& d = probs[(size_t)q];
-    cost[(size_t)q] = (path == CSX_PATH_MOMENT) ? (double)ncell_h[d.conf] + 8.0 * d.P : (double)d.P;
-  }
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-
-  char* db = (char*)scratch(SCR_FIT_DESC, (size_t)nprob * (sizeof(ProbDesc) + sizeof(int)) + 64, &rc);
+  const bool device_order = nconf <= FIT_ORDER_MAX;
+  const size_t desc_b = ((size_t)nprob * sizeof(ProbDesc) + 255) & ~size_t(255);
+  const size_t order_b = ((size_t)nprob * sizeof(int) + 255) & ~size_t(255);
+  char* db = (char*)scratch(SCR_FIT_DESC, desc_b + order_b + 256 + (size_t)nconf * 3 * sizeof(int), &rc);
   if (rc) return rc;
   ProbDesc* probs_d = (ProbDesc*)db;
-  int* order_d = (int*)(db + (size_t)nprob * sizeof(ProbDesc));
-  int* head_d = order_d + nprob;
-  CSX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), (size_t)nprob * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
-  CSX_CUDA(cudaMemcpyAsync(order_d, order.data(), (size_t)nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+  int* order_d = (int*)(db + desc_b);
+  int* head_d = (int*)(db + desc_b + order_b);
+  int* Kdev = (int*)(db + desc_b + order_b + 256);
+  int *perm = nullptr, *coffs = nullptr, *ncell = nullptr;
+  {
+    TraceSpan tr("fit: descriptors + cells", s);
+    CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+    if ((rc = launch_fit_desc(nconf, sky->nreal, Kdev, probs_d, s))) return rc;
+    if (path == CSX_PATH_MOMENT) {
+      const size_t per = (size_t)npix;
+      char* cb = (char*)scratch(SCR_CELLS, (size_t)nconf * (2 * per + 2) * sizeof(int) + 256, &rc);
+      if (rc) return rc;
+      perm = (int*)cb;
+      coffs = perm + (size_t)nconf * per;
+      ncell = coffs + (size_t)nconf * (per + 1);
+      if ((rc = launch_cells(npix, nconf, labels, Kdev, perm, coffs, ncell, s))) return rc;
+    }
+    if (device_order) {
+      if ((rc = launch_fit_order(nconf, sky->nreal, Kdev, ncell, order_d, s))) return rc;
+    } else {
+      // longest-first queue order from the host-known estimate (more configurations than the
+      // device sort takes)
+      std::vector<int> order((size_t)nprob);
+      std::iota(order.begin(), order.end(), 0);
+      const int nr = sky->nreal;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return cost[(size_t)(x / nr)] > cost[(size_t)(y / nr)]; });
+      CSX_CUDA(cudaMemcpyAsync(order_d, order.data(), (size_t)nprob * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+  }
 
   long long slot_floats = 0;
   fit_slot_floats(Pmax, rows_max, ncell_max, o.history, path, &slot_floats);
@@ -514,6 +574,90 @@ int csx_fit_batch(const csx_model* m, const csx_sky* sky, int32_t nconf, const i
   return launch_fit(a, o.threads, grid, s);
 }
 
+int csx_cell_like_grad(const csx_model* m, const csx_sky* sky, const int32_t* labels,
+                       const int32_t K[3], int32_t nprob, const float* beta_ref, const float* beta,
+                       double* L, float* grad, void* stream) {
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (!K) return fail(CSX_EINVAL, "K is NULL");
+  if ((rc = check_K(K))) return rc;
+  if (sky->noise_kind == CSX_NOISE_PERPIXEL)
+    return fail(CSX_EINVAL, "the cell-moment evaluation needs homogeneous or separable noise");
+  if (nprob < 0 || nprob > sky->nreal) return fail(CSX_EINVAL, "nprob must be in [0, sky->nreal]");
+  if (nprob == 0) return CSX_OK;
+  if (!beta_ref || !beta || !L || !grad) return fail(CSX_EINVAL, "NULL argument");
+  if (sky->npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  CSX_ALIGN(labels, 4);
+  CSX_ALIGN(beta_ref, 4);
+  CSX_ALIGN(beta, 4);
+  CSX_ALIGN(L, 8);
+  CSX_ALIGN(grad, 4);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int npix = sky->npix;
+  const int P = K[0] + K[1] + K[2];
+  const int rows = K[0] + 2 * K[1] + K[2];
+  const int Pmax = (P + 3) & ~3;
+  const int bound = (int)std::min<long long>((long long)npix, (long long)K[0] * K[1] * K[2]);
+  char* cb = (char*)scratch(SCR_CELLS, (size_t)(2 * npix + 2) * sizeof(int) + 256, &rc);
+  if (rc) return rc;
+  int* perm = (int*)cb;
+  int* coffs = perm + npix;
+  int* ncell = coffs + npix + 1;
+  int* Kdev = (int*)(cb + (((size_t)(2 * npix + 2) * sizeof(int) + 15) & ~size_t(15)));
+  std::vector<ProbDesc> probs((size_t)nprob);
+  for (int q = 0; q < nprob; ++q) {
+    ProbDesc& d = probs[(size_t)q];
+    d.conf = 0;
+    d.real = q;
+    d.Kd = K[0];
+    d.KT = K[1];
+    d.Ks = K[2];
+    d.P = P;
+    d.poff = (long long)q * P;
+    d.toff = 0;
+  }
+  ProbDesc* probs_d = (ProbDesc*)scratch(SCR_FIT_DESC, (size_t)nprob * sizeof(ProbDesc), &rc);
+  if (rc) return rc;
+  long long slot_floats = 0;
+  fit_slot_floats(Pmax, rows, bound, 1, CSX_PATH_MOMENT, &slot_floats);
+  int grid = 0;
+  if ((rc = fit_grid(128, CSX_PATH_MOMENT, CSX_GRAD_ADJOINT, CSX_SOLVER_LBFGS, &grid))) return rc;
+  if (grid > nprob) grid = nprob;
+  float* slots = (float*)scratch(SCR_FIT_SLOTS, (size_t)grid * slot_floats * sizeof(float), &rc);
+  if (rc) return rc;
+  CSX_CUDA(cudaMemcpyAsync(Kdev, K, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+  CSX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), (size_t)nprob * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  if ((rc = launch_cells(npix, 1, labels, Kdev, perm, coffs, ncell, s))) return rc;
+  FitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = make_bands(*m);
+  a.npix = npix;
+  a.nreal = sky->nreal;
+  a.noise_kind = sky->noise_kind;
+  a.d = sky->d;
+  a.w = sky->w;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.labels = labels;
+  a.perm = perm;
+  a.cell_off = coffs;
+  a.ncell = ncell;
+  a.probs = probs_d;
+  a.nprob = nprob;
+  a.beta0 = beta_ref;
+  a.beta_eval = beta;
+  a.L_out = L;
+  a.grad_out = grad;
+  a.slots = slots;
+  a.slot_floats = slot_floats;
+  a.Pmax = Pmax;
+  a.rows_max = rows;
+  a.ncell_max = bound;
+  a.history = 1;
+  a.path = CSX_PATH_MOMENT;
+  return launch_cell_eval(a, grid, s);
+}
+
 int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const int32_t* labels,
                     const int32_t* K, const float* beta, const float* d_fg, float* s_hat,
                     float* sigma2, float* r_sys, double* metrics, void* stream) {
@@ -533,30 +677,22 @@ int csx_reconstruct(const csx_model* m, const csx_sky* sky, int32_t nconf, const
   CSX_ALIGN(r_sys, 4);
   CSX_ALIGN(metrics, 8);
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<ProbDesc> probs((size_t)nprob);
-  long long poff = 0, toff = 0;
+  // descriptors formed on the device from K (no pageable per-problem copy, so the call does not
+  // wait for earlier work on the stream)
+  long long toff = 0;
   for (int c = 0; c < nconf; ++c) {
     if ((rc = check_K(K + 3 * c))) return rc;
-    for (int n = 0; n < sky->nreal; ++n) {
-      ProbDesc& d = probs[(size_t)c * sky->nreal + n];
-      d.conf = c;
-      d.real = n;
-      d.Kd = K[3 * c];
-      d.KT = K[3 * c + 1];
-      d.Ks = K[3 * c + 2];
-      d.P = d.Kd + d.KT + d.Ks;
-      d.poff = poff;
-      d.toff = toff;
-      poff += d.P;
-      toff += d.Kd + 2 * d.KT + d.Ks;
-    }
+    toff += (long long)sky->nreal * ((long long)K[3 * c] + 2LL * K[3 * c + 1] + K[3 * c + 2]);
   }
-  char* db = (char*)scratch(SCR_RECON_DESC, (size_t)nprob * sizeof(ProbDesc), &rc);
+  const size_t desc_b = ((size_t)nprob * sizeof(ProbDesc) + 255) & ~size_t(255);
+  char* db = (char*)scratch(SCR_RECON_DESC, desc_b + (size_t)nconf * 3 * sizeof(int), &rc);
   if (rc) return rc;
   ProbDesc* probs_d = (ProbDesc*)db;
+  int* Kdev = (int*)(db + desc_b);
   float* tables = (float*)scratch(SCR_TABLES, (size_t)toff * NB * sizeof(float), &rc);
   if (rc) return rc;
-  CSX_CUDA(cudaMemcpyAsync(probs_d, probs.data(), (size_t)nprob * sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+  CSX_CUDA(cudaMemcpyAsync(Kdev, K, (size_t)nconf * 3 * sizeof(int), cudaMemcpyHostToDevice, s));
+  if ((rc = launch_fit_desc(nconf, sky->nreal, Kdev, probs_d, s))) return rc;
   const Bands b = make_bands(*m);
   if ((rc = launch_recon_tables(b, (int)nprob, probs_d, beta, tables, toff, s))) return rc;
   if (metrics) CSX_CUDA(cudaMemsetAsync(metrics, 0, (size_t)nprob * CSX_NMETRIC * sizeof(double), s));

@@ -306,6 +306,63 @@ __device__ __forceinline__ void warp_run_add3(float* acc0, int k0, float v0, flo
 }
 
 // ---------------------------------------------------------------------------------------------
+// Deterministic variant of warp_run_add3 for a warp-private accumulator `acc` (a P-vector that no
+// other warp writes): keys are indices into acc (three disjoint ranges), -1 = nothing to add.
+// Runs of equal keys in consecutive lanes are combined by the same segmented shuffle scan; the run
+// totals are then added in a fixed order. Totals with distinct keys are added at once; when several
+// runs of one warp end on the same key (a label that reappears after another one), the lowest such
+// lane adds their totals in increasing lane order. The result is independent of scheduling, so a
+// reduction built from it gives the same bits on every run. `stage` holds 32 floats of this warp.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void warp_put_ordered(float* acc, int key, float v, bool end,
+                                                 float* stage) {
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(full, end ? key : -1 - lane);
+  if (!__any_sync(full, end && (grp & (grp - 1u)) != 0u)) {
+    if (end) acc[key] += v;
+    return;
+  }
+  stage[lane] = v;
+  __syncwarp();
+  if (end && (grp & ((1u << lane) - 1u)) == 0u) {
+    float t = 0.f;
+    for (unsigned m = grp; m; m &= m - 1u) t += stage[__ffs(m) - 1];
+    acc[key] += t;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void warp_run_accum3(float* acc, int k0, float v0, int k1, float v1,
+                                                int k2, float v2, float* stage) {
+  constexpr unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned upto = (2u << lane) - 1u;
+  const int p0 = __shfl_up_sync(full, k0, 1), p1 = __shfl_up_sync(full, k1, 1),
+            p2 = __shfl_up_sync(full, k2, 1);
+  const unsigned h0 = __ballot_sync(full, lane == 0 || k0 != p0);
+  const unsigned h1 = __ballot_sync(full, lane == 0 || k1 != p1);
+  const unsigned h2 = __ballot_sync(full, lane == 0 || k2 != p2);
+  const int s0 = 31 - __clz(h0 & upto), s1 = 31 - __clz(h1 & upto), s2 = 31 - __clz(h2 & upto);
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float t0 = __shfl_up_sync(full, v0, d), t1 = __shfl_up_sync(full, v1, d),
+                t2 = __shfl_up_sync(full, v2, d);
+    if (lane - d >= s0) v0 += t0;
+    if (lane - d >= s1) v1 += t1;
+    if (lane - d >= s2) v2 += t2;
+  }
+  const bool last = lane == 31;
+  const bool e0 = k0 >= 0 && (last || ((h0 >> (lane + 1)) & 1u));
+  const bool e1 = k1 >= 0 && (last || ((h1 >> (lane + 1)) & 1u));
+  const bool e2 = k2 >= 0 && (last || ((h2 >> (lane + 1)) & 1u));
+  warp_put_ordered(acc, k0, v0, e0, stage);
+  warp_put_ordered(acc, k1, v1, e1, stage);
+  warp_put_ordered(acc, k2, v2, e2, stage);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------------------------
 // Block reductions: every thread of the block receives the total. `sbuf` holds NT/32 values.
 // ---------------------------------------------------------------------------------------------
 template <typename T>

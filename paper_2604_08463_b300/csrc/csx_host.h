@@ -38,6 +38,11 @@ void scratch_release_all();
 
 Bands make_bands(const csx_model& m);
 
+// Argument checks shared by the entry points (CSX_EINVAL with a message on failure).
+int check_model(const csx_model* m);
+int check_sky(const csx_sky* s, int nfreq);
+int check_K(const int32_t* K);  // 1 <= K_j <= CSX_MAX_K
+
 // ---- problem descriptor of the fit / reconstruction ---------------------------------------------
 struct ProbDesc {
   int conf, real;
@@ -63,11 +68,40 @@ struct SpecArgs {
 };
 int launch_tables(const Bands& b, int nprob, int Kd, int KT, int Ks, const float* beta,
                   float* tables, cudaStream_t s);
+
+// All-FP64 evaluation (k_spectral64.cu): the per-band constants in double.
+struct Bands64 {
+  int nf;
+  double xk0;
+  double lnd[NB], lns[NB], xk[NB], cd[NB], cs[NB];
+};
+Bands64 make_bands64(const csx_model& m);
+struct Spec64Args {
+  Bands64 bands;
+  int npix, nprob, Kd, KT, Ks, P, rows;
+  int noise_kind;
+  const float* d;
+  const float* w;
+  const float* ninv_pix;
+  float ninv_band[NB];
+  const int* labels;
+  const double* beta;
+  double* tables;   // [nprob][rows][16]
+  double* L;
+  double* grad;     // NULL: likelihood only
+};
+int launch_spectral64(const Spec64Args& a, bool grad, cudaStream_t s);
 int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA, cudaStream_t s);
 int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s);
+// Synchronises `s`, returns (and clears) the count of bounded device waits that gave up.
+int device_timeouts(cudaStream_t s, unsigned* count);
 
 int launch_cells(int npix, int nconf, const int* labels, const int* K_dev, int* perm,
                  int* cell_off, int* ncell, cudaStream_t s);
+constexpr int FIT_ORDER_MAX = 16384;  // configurations ordered on the device by launch_fit_order
+int launch_fit_order(int nconf, int nreal, const int* K_dev, const int* ncell, int* order,
+                     cudaStream_t s);
+int launch_fit_desc(int nconf, int nreal, const int* K_dev, ProbDesc* probs, cudaStream_t s);
 
 constexpr int KMEANS_KMAX = 2048;
 size_t kmeans_smem(int kmax);
@@ -104,8 +138,11 @@ struct FitArgs {
   float lower[3], upper[3], xtol[3], fd_step;
   int solver;
   float topk;
+  const float* beta_eval;  // launch_cell_eval: evaluation points (beta0 holds the reference points)
+  float* grad_out;         // launch_cell_eval: gradients [nprob][P]
 };
 int launch_fit(const FitArgs& a, int threads, int grid, cudaStream_t s);
+int launch_cell_eval(const FitArgs& a, int grid, cudaStream_t s);
 int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path,
                     long long* out);
 int fit_grid(int threads, int path, int grad_mode, int solver, int* grid);

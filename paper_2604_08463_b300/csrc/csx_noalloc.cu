@@ -10,7 +10,6 @@
 // nothing. Inputs and outputs are still the caller's buffers.
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -31,13 +30,21 @@ std::mutex g_mu;
 float* g_dev_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_tables on the current device. In host code the symbol's name is only
-// a host-side handle, so the address is looked up once per device (with that device current).
-int table_buffer(float** out) {
+// a host-side handle, so the address is looked up with that device current: on the first call on
+// the device, and again on every call made while `stream` is not capturing, so that a context that
+// was torn down and re-created (cudaDeviceReset) gets its own module's address. During a capture
+// the address found by an earlier call is used; the first call on a device must not be captured.
+int table_buffer(cudaStream_t stream, float** out) {
   int dev = 0;
   CSX_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return fail(CSX_EINVAL, "device index out of range");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CSX_CUDA(cudaStreamIsCapturing(stream, &cap));
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_dev_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_dev_ptr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(CSX_EINVAL, "csx_spectral_grad_noalloc: the first call on a device must not be "
+                              "made during a stream capture");
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tables);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_tables)");
@@ -56,55 +63,35 @@ extern "C" int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky,
                                          const int32_t* labels, const int32_t K[3],
                                          int32_t nprob, const float* beta, double* L,
                                          float* grad, void* stream) {
-  if (!m) return fail(CSX_EINVAL, "model is NULL");
-  if (m->nfreq < 1 || m->nfreq > 15) return fail(CSX_EINVAL, "nfreq must be in 1..15");
-  if (m->units != 0 && m->units != 1) return fail(CSX_EINVAL, "units must be 0 (K_CMB) or 1 (RJ)");
-  if (!(m->nu0_dust_ghz > 0) || !(m->nu0_sync_ghz > 0) || (m->units == 0 && !(m->t_cmb > 0)))
-    return fail(CSX_EINVAL, "reference frequencies and t_cmb must be > 0");
-  for (int f = 0; f < m->nfreq; ++f)
-    if (!(m->nu_ghz[f] > 0)) return fail(CSX_EINVAL, "band frequencies must be > 0");
-  if (!sky) return fail(CSX_EINVAL, "sky is NULL");
-  if (sky->npix < 0 || sky->nreal < 0) return fail(CSX_EINVAL, "npix and nreal must be >= 0");
-  if (sky->noise_kind < 0 || sky->noise_kind > 2) return fail(CSX_EINVAL, "unknown noise_kind");
-  if (sky->npix > 0 && sky->nreal > 0 && !sky->d) return fail(CSX_EINVAL, "sky->d is NULL");
-  if (sky->noise_kind == CSX_NOISE_SEPARABLE && sky->npix > 0 && !sky->w)
-    return fail(CSX_EINVAL, "separable noise needs sky->w");
-  if (sky->noise_kind == CSX_NOISE_PERPIXEL && sky->npix > 0 && !sky->ninv_pix)
-    return fail(CSX_EINVAL, "per-pixel noise needs sky->ninv_pix");
-  {
-    int rc0;
-    if ((rc0 = check_align(sky->d, 16, "sky->d")) || (rc0 = check_align(sky->ninv_pix, 16, "sky->ninv_pix")) ||
-        (rc0 = check_align(sky->w, 4, "sky->w")) || (rc0 = check_align(labels, 4, "labels")) ||
-        (rc0 = check_align(beta, 4, "beta")) || (rc0 = check_align(L, 8, "L")) ||
-        (rc0 = check_align(grad, 4, "grad")))
-      return rc0;
-  }
-  if (sky->noise_kind != CSX_NOISE_PERPIXEL)
-    for (int f = 0; f < m->nfreq; ++f)
-      if (!(sky->ninv_band[f] >= 0.f) || !std::isfinite(sky->ninv_band[f]))
-        return fail(CSX_EINVAL, "ninv_band must be finite and >= 0");
-  if (!K || K[0] < 1 || K[1] < 1 || K[2] < 1) return fail(CSX_EINVAL, "every K_j must be >= 1");
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (!K) return fail(CSX_EINVAL, "K is NULL");
+  if ((rc = check_K(K))) return rc;
+  if ((rc = check_align(labels, 4, "labels")) || (rc = check_align(beta, 4, "beta")) ||
+      (rc = check_align(L, 8, "L")) || (rc = check_align(grad, 4, "grad")))
+    return rc;
   if (nprob < 0 || nprob > sky->nreal) return fail(CSX_EINVAL, "nprob must be in [0, sky->nreal]");
   if (nprob == 0) return CSX_OK;
   if (!beta || !L || !grad || (sky->npix > 0 && !labels))
     return fail(CSX_EINVAL, "beta, L, grad and labels must not be NULL");
-  const int P = K[0] + K[1] + K[2];
-  const int rows = K[0] + 2 * K[1] + K[2];
-  const size_t need = (size_t)nprob * rows * NB;
-  if (need > kNoAllocTableFloats)
+  // sizes in 64-bit arithmetic (K_j <= CSX_MAX_K keeps P and the row count within int)
+  const long long P = (long long)K[0] + K[1] + K[2];
+  const long long rows = (long long)K[0] + 2LL * K[1] + K[2];
+  const long long need = (long long)nprob * rows * NB;
+  if (need > (long long)kNoAllocTableFloats)
     return fail(CSX_EINVAL, "csx_spectral_grad_noalloc: nprob x (K_d + 2 K_T + K_s) x 16 = " +
                                 std::to_string(need) + " table floats exceed the static buffer of " +
                                 std::to_string(kNoAllocTableFloats) +
                                 "; split the problems over several calls or use csx_spectral_grad");
-  float* tables = nullptr;
-  int rc = table_buffer(&tables);
-  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  float* tables = nullptr;
+  if ((rc = table_buffer(s, &tables))) return rc;
   const Bands b = make_bands(*m);
   // the tables are fully rewritten; L and grad are accumulated and so start from zero
   if ((rc = launch_tables(b, nprob, K[0], K[1], K[2], beta, tables, s))) return rc;
   CSX_CUDA(cudaMemsetAsync(L, 0, (size_t)nprob * sizeof(double), s));
-  CSX_CUDA(cudaMemsetAsync(grad, 0, (size_t)nprob * P * sizeof(float), s));
+  CSX_CUDA(cudaMemsetAsync(grad, 0, (size_t)nprob * (size_t)P * sizeof(float), s));
   if (sky->npix == 0) return CSX_OK;
   SpecArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -114,8 +101,8 @@ extern "C" int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky,
   a.Kd = K[0];
   a.KT = K[1];
   a.Ks = K[2];
-  a.P = P;
-  a.rows = rows;
+  a.P = (int)P;
+  a.rows = (int)rows;
   a.noise_kind = sky->noise_kind;
   a.d = sky->d;
   a.w = sky->w;

@@ -147,6 +147,123 @@ __global__ void __launch_bounds__(CELL_NT) k_cells(int npix, const int* __restri
   }
 }
 
+// Work-queue order of the persistent fit, longest first: configurations sorted by the cost
+// estimate ncell + 8 P (descending; ties by configuration index; a configuration with a bad label,
+// ncell < 0, costs 0 and goes last), each expanded to its nreal problems c * nreal + n. One CTA,
+// bitonic sort of (cost, index) keys in shared memory, nconf <= FIT_ORDER_MAX.
+constexpr int ORDER_NT = 1024;
+
+__global__ void __launch_bounds__(ORDER_NT) k_fit_order(int nconf, int nreal,
+                                                        const int* __restrict__ Kdev,
+                                                        const int* __restrict__ ncell,
+                                                        int* __restrict__ order) {
+  extern __shared__ unsigned long long okey[];
+  int n2 = 1;
+  while (n2 < nconf) n2 <<= 1;
+  for (int i = threadIdx.x; i < n2; i += ORDER_NT) {
+    unsigned long long k = ~0ULL;  // padding sorts last
+    if (i < nconf) {
+      const long long cost = (ncell ? (long long)max(ncell[i], 0) : 0LL) +
+                             8LL * ((long long)Kdev[3 * i] + Kdev[3 * i + 1] + Kdev[3 * i + 2]);
+      const unsigned inv = 0x7fffffffu - (unsigned)min(cost, 0x7fffffffLL);
+      k = ((unsigned long long)inv << 32) | (unsigned)i;
+    }
+    okey[i] = k;
+  }
+  __syncthreads();
+  for (int size = 2; size <= n2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += ORDER_NT) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const unsigned long long a = okey[i], b = okey[j];
+          if ((a > b) == up) {
+            okey[i] = b;
+            okey[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (long long t = threadIdx.x; t < (long long)nconf * nreal; t += ORDER_NT) {
+    const int rank = (int)(t / nreal), r = (int)(t % nreal);
+    const int c = (int)(okey[rank] & 0xffffffffu);
+    order[t] = c * nreal + r;
+  }
+}
+
+// Problem descriptors of the fit and the reconstruction: problem q = c * nreal + n; its parameters
+// start at nreal * coff[c] + n * P_c (coff the exclusive prefix sum of P_c) and its SED tables at
+// row nreal * roff[c] + n * rows_c (roff that of rows_c = K_d + 2 K_T + K_s). One CTA.
+constexpr int DESC_NT = 1024;
+
+__global__ void __launch_bounds__(DESC_NT) k_fit_desc(int nconf, int nreal, const int* __restrict__ Kdev,
+                                                      ProbDesc* __restrict__ probs) {
+  __shared__ long long part[DESC_NT], rpart[DESC_NT];
+  const int chunk = (nconf + DESC_NT - 1) / DESC_NT;
+  const int c0 = min(nconf, (int)threadIdx.x * chunk), c1 = min(nconf, c0 + chunk);
+  long long sum = 0, rsum = 0;
+  for (int c = c0; c < c1; ++c) {
+    sum += (long long)Kdev[3 * c] + Kdev[3 * c + 1] + Kdev[3 * c + 2];
+    rsum += (long long)Kdev[3 * c] + 2LL * Kdev[3 * c + 1] + Kdev[3 * c + 2];
+  }
+  part[threadIdx.x] = sum;
+  rpart[threadIdx.x] = rsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long run = 0, rrun = 0;
+    for (int t = 0; t < DESC_NT; ++t) {
+      const long long v = part[t], rv = rpart[t];
+      part[t] = run;
+      rpart[t] = rrun;
+      run += v;
+      rrun += rv;
+    }
+  }
+  __syncthreads();
+  long long coff = part[threadIdx.x], roff = rpart[threadIdx.x];
+  for (int c = c0; c < c1; ++c) {
+    const int kd = Kdev[3 * c], kt = Kdev[3 * c + 1], ks = Kdev[3 * c + 2];
+    const int P = kd + kt + ks, rows = kd + 2 * kt + ks;
+    for (int n = 0; n < nreal; ++n) {
+      ProbDesc d;
+      d.conf = c;
+      d.real = n;
+      d.Kd = kd;
+      d.KT = kt;
+      d.Ks = ks;
+      d.P = P;
+      d.poff = (long long)nreal * coff + (long long)n * P;
+      d.toff = (long long)nreal * roff + (long long)n * rows;
+      probs[(long long)c * nreal + n] = d;
+    }
+    coff += P;
+    roff += rows;
+  }
+}
+
+int launch_fit_desc(int nconf, int nreal, const int* K_dev, ProbDesc* probs, cudaStream_t s) {
+  if (nconf == 0 || nreal == 0) return CSX_OK;
+  k_fit_desc<<<1, DESC_NT, 0, s>>>(nconf, nreal, K_dev, probs);
+  CSX_CUDA(cudaGetLastError());
+  return CSX_OK;
+}
+
+int launch_fit_order(int nconf, int nreal, const int* K_dev, const int* ncell, int* order,
+                     cudaStream_t s) {
+  if (nconf == 0 || nreal == 0) return CSX_OK;
+  if (nconf > FIT_ORDER_MAX) return fail(CSX_EINVAL, "too many configurations for the device order");
+  int n2 = 1;
+  while (n2 < nconf) n2 <<= 1;
+  const size_t smem = (size_t)n2 * sizeof(unsigned long long);
+  CSX_CUDA(cudaFuncSetAttribute(k_fit_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(FIT_ORDER_MAX * sizeof(unsigned long long))));
+  k_fit_order<<<1, ORDER_NT, smem, s>>>(nconf, nreal, K_dev, ncell, order);
+  CSX_CUDA(cudaGetLastError());
+  return CSX_OK;
+}
+
 int launch_cells(int npix, int nconf, const int* labels, const int* K_dev, int* perm, int* cell_off,
                  int* ncell, cudaStream_t s) {
   if (nconf == 0) return CSX_OK;

@@ -58,6 +58,7 @@ struct Ctx {
   const float* d;     // [npix][2][16] of the realization
   float *z, *g, *p, *zt, *gt, *hs, *x, *gacc, *hacc, *S, *Y, *tab, *mom;
   float *tabr, *xr;   // moment path: SED tables and parameters of the reference point
+  float *gw, *hw;     // warp-private partial gradients / Gauss-Newton diagonals [warps][P]
   int* trip;
   float* smem;        // moment path: dynamic shared memory (build staging, then per-thread rows)
 };
@@ -66,7 +67,41 @@ struct Shared {
   double red[16];
   double rho[MAXM], alpha[MAXM];
   float gacc[SMEM_P], hacc[SMEM_P];
+  float stage[8][32];  // per-warp staging of warp_run_accum3
+  int cmd;             // the L-BFGS leader warp's request to the CTA (FitCmd)
 };
+
+// Gradient (and Gauss-Newton diagonal) accumulation without float atomics: each warp adds its
+// run totals to its own partial P-vector in program order (warp_run_accum3), and the vectors are
+// summed in warp order at the end of the evaluation, so every evaluation of the same point gives
+// the same bits.
+template <int NT>
+__device__ __forceinline__ void partials_zero(const Ctx& c, bool want_h) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* gw = c.gw + (long long)warp * c.P;
+  float* hw = c.hw + (long long)warp * c.P;
+  for (int i = lane; i < c.P; i += 32) {
+    gw[i] = 0.f;
+    if (want_h) hw[i] = 0.f;
+  }
+  __syncwarp();
+}
+
+template <int NT>
+__device__ __forceinline__ void partials_reduce(const Ctx& c, bool want_h) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < c.P; i += NT) {
+    float g = c.gw[i], h = want_h ? c.hw[i] : 0.f;
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      g += c.gw[(long long)w * c.P + i];
+      if (want_h) h += c.hw[(long long)w * c.P + i];
+    }
+    c.gacc[i] = g;
+    if (want_h) c.hacc[i] = h;
+  }
+  __syncthreads();
+}
 
 __device__ __forceinline__ int ptype(const Ctx& c, int i) {
   return i < c.Kd ? 0 : (i < c.Kd + c.KT ? 1 : 2);
@@ -91,12 +126,43 @@ __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, floa
 // block is small where it has to be: R and C carry residuals, not the foreground signal.
 //
 // One warp per cell. Phase 1, lane = pixel: the cell's Gram-Schmidt basis of A_r (computed once per
-// cell, the noise weight w_p scales out of s and r), then s and r of up to 32 pixels into shared
-// memory. Phase 2: lanes = 15 upper 4x4 blocks of the 20x20 (zero-padded) v v^T x 2 pixel groups;
+// cell, the noise weight w_p scales out of s and r), then s by back-substitution and r = d - A_r s
+// formed without the data's rounding (resid_exact) of up to 32 pixels into shared memory. Phase 2: lanes = 15 upper 4x4 blocks of the 20x20 (zero-padded) v v^T x 2 pixel groups;
 // partial sums are flushed every 16 pixels to bound FP32 rounding growth. Also sum w d^T n d.
 constexpr int NM = 171;          // stored moment entries per cell
 constexpr int VROW = 44;         // shared floats per pixel: v_Q[20], v_U[20], w (16-byte rows)
-constexpr int BUILD_SMEM_PER_WARP = 32 * VROW + 32;  // pixel rows + the cell's basis
+constexpr int BUILD_SMEM_PER_WARP = 32 * VROW + 64;  // pixel rows + the cell's basis and columns
+
+// d - (s0 + a1 s1 + a2 s2) for FP32 inputs, rounded once: the products are split exactly (FMA
+// residue) and the sum is carried with its rounding errors (TwoSum), so the signal-sized terms cancel
+// without leaving their rounding in the small result. The reference-point decomposition
+// d = A_r s + r of the cell moments is then exact to the rounding of r itself, and the gradient
+// formed from the moments at the reference point is as accurate as the residuals, not the data.
+// (__fmul_rn / __fadd_rn are never contracted into FMAs, which would break the error terms.)
+__device__ __forceinline__ void two_sum_acc(float& x, float b, float& err) {
+  const float sum = __fadd_rn(x, b);
+  const float bb = __fsub_rn(sum, x);
+  err = __fadd_rn(err, __fadd_rn(__fsub_rn(x, __fsub_rn(sum, bb)), __fsub_rn(b, bb)));
+  x = sum;
+}
+__device__ __forceinline__ float resid_exact(float d, float s0, float s1, float s2, float a1,
+                                             float a2) {
+  const float p1 = __fmul_rn(a1, s1), e1 = fmaf(a1, s1, -p1);
+  const float p2 = __fmul_rn(a2, s2), e2 = fmaf(a2, s2, -p2);
+  float x = d, err = 0.f;
+  two_sum_acc(x, -p1, err);
+  two_sum_acc(x, -p2, err);
+  two_sum_acc(x, -s0, err);
+  return __fadd_rn(x, __fsub_rn(err, __fadd_rn(e1, e2)));
+}
+
+// Floats of the per-thread evaluation rows at the start of the dynamic shared memory (moment path:
+// N A_1 and N A_2 per thread, plus the staged moments with CSX_FIT_STAGE_MOMENTS); the warp
+// partials of the gradient follow them.
+template <int NT, int PATH>
+constexpr int fit_rows_floats() {
+  return PATH == CSX_PATH_MOMENT ? (30 + (CSX_FIT_STAGE_MOMENTS ? NM : 0)) * NT : 0;
+}
 
 __device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
 
@@ -104,7 +170,7 @@ template <int NT, bool SEP>
 __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* sv = smem + warp * BUILD_SMEM_PER_WARP;  // 32 pixel rows
-  float* sb = sv + 32 * VROW;                      // the cell's basis c1[16], c2[16]
+  float* sb = sv + 32 * VROW;  // the cell's basis c1[16], c2[16] and columns A_d[16], A_s[16]
   const int grp = lane / 15, blk = lane % 15;
   // upper-triangle 4x4 blocks of a 5x5 block grid: (ba, bb), ba <= bb
   int ba = 0, rem = blk;
@@ -143,6 +209,8 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
       if (lane < 16) {
         sb[f] = c1f;
         sb[16 + f] = c2f;
+        sb[32 + f] = adf;
+        sb[48 + f] = asf;
       }
       __syncwarp();
     }
@@ -174,19 +242,21 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
         dnd += (double)(wp * pd);
         tq0 *= g.i0; tq1 *= g.i1; tq2 *= g.i2;
         tu0 *= g.i0; tu1 *= g.i1; tu2 *= g.i2;
+        // s = R^-1 t (Gram-Schmidt back-substitution), then r = d - A_r s exactly for this s
+        const float sq1 = fmaf(-g.nu, tq2, tq1), su1 = fmaf(-g.nu, tu2, tu1);
+        const float sq0 = tq0 - g.mu1 * sq1 - g.mu2 * tq2;
+        const float su0 = tu0 - g.mu1 * su1 - g.mu2 * tu2;
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
-          const float c1 = sb[f], c2 = sb[16 + f];
-          row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2, fmaf(tq1, c1, tq0)) : 0.f;
-          row[20 + f] = (f < 15) ? du[f] - fmaf(tu2, c2, fmaf(tu1, c1, tu0)) : 0.f;
+          const float a1 = sb[32 + f], a2 = sb[48 + f];
+          row[f] = (f < 15) ? resid_exact(dq[f], sq0, sq1, tq2, a1, a2) : 0.f;
+          row[20 + f] = (f < 15) ? resid_exact(du[f], su0, su1, tu2, a1, a2) : 0.f;
         }
-        // s = R^-1 t (Gram-Schmidt back-substitution)
-        const float sq1 = fmaf(-g.nu, tq2, tq1), su1 = fmaf(-g.nu, tu2, tu1);
-        row[15] = tq0 - g.mu1 * sq1 - g.mu2 * tq2;
+        row[15] = sq0;
         row[16] = sq1;
         row[17] = tq2;
         row[18] = row[19] = 0.f;
-        row[35] = tu0 - g.mu1 * su1 - g.mu2 * tu2;
+        row[35] = su0;
         row[36] = su1;
         row[37] = tu2;
         row[38] = row[39] = 0.f;
@@ -259,10 +329,7 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
 // into hacc). Per-thread rows in shared memory (stride NT): N A_1, N A_2 and R N A (75 floats).
 template <int NT, bool WANT_H>
 __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
-  for (int i = threadIdx.x; i < c.P; i += NT) {
-    c.gacc[i] = 0.f;
-    if (WANT_H) c.hacc[i] = 0.f;
-  }
+  partials_zero<NT>(c, WANT_H);
   fill_tables<NT>(a, c, c.x, c.tab);  // ends with a barrier
   const float* nb = a.ninv_band;
   float nsum = 0.f;
@@ -276,8 +343,19 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
   const int mst = c.ncell;
 #endif
   float acc = 0.f;  // per-thread sum over its few cells in FP32, FP64 across the block
-  for (int cell = threadIdx.x; cell < c.ncell; cell += NT) {
-    const int kd = c.trip[cell], kt = c.trip[c.ncell + cell], ks = c.trip[2 * c.ncell + cell];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* gwv = c.gw + (long long)warp * c.P;
+  float* hwv = c.hw + (long long)warp * c.P;
+  // warp-uniform trip count: lane l of a warp takes cell base + l (consecutive cells, so the
+  // warp's run scan combines the cells of one patch)
+  for (int base = threadIdx.x & ~31; base < c.ncell; base += NT) {
+    const int cell = base + lane;
+    int kd = -1, kt = -1, ks = -1;
+    float gbd = 0.f, gtd = 0.f, gbs = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f;
+    if (cell < c.ncell) do {
+    kd = c.trip[cell];
+    kt = c.trip[c.ncell + cell];
+    ks = c.trip[2 * c.ncell + cell];
     const float* pd = c.tab + kd * NB;
     const float* bt = c.tab + (c.Kd + kt) * NB;
     const float* dt = c.tab + (c.Kd + c.KT + kt) * NB;
@@ -341,7 +419,8 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
       acc += nan_f();
-      continue;
+      kd = kt = ks = -1;
+      break;
     }
     float v[3][3];
     chol3_inverse(ch, v[0][0], v[0][1], v[0][2], v[1][1], v[1][2], v[2][2]);
@@ -385,7 +464,6 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     // E = U + C Z + B - A Psi, the B term of E M^-1 in band i is sum_l B[i][l] M^-1[l][k]
     float trNR = 0.f;
     float AtRA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    float gbd = 0.f, gtd = 0.f, gbs = 0.f;
 #pragma unroll 1
     for (int i = 0; i < 15; ++i) {
       float b0 = 0.f, b1 = 0.f, b2 = 0.f;
@@ -461,9 +539,9 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       gtd = fmaf(t1, dt[f], gtd);
       gbs = fmaf(F2 * row[(15 + f) * NT], a.bands.lns[f], gbs);
     }
-    atomicAdd(c.gacc + kd, -2.f * gbd);
-    atomicAdd(c.gacc + c.Kd + kt, -2.f * gtd);
-    atomicAdd(c.gacc + c.Kd + c.KT + ks, -2.f * gbs);
+    gbd *= -2.f;
+    gtd *= -2.f;
+    gbs *= -2.f;
     if (WANT_H) {
       // Gauss-Newton diagonal 2 (sum w s_k^2) da^T N da (the scaling of the optimiser's variables;
       // the same quantity as the streaming path's), with sum w s s^T at the reference point (Q)
@@ -475,14 +553,16 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) n2[k] = fmaf(nb[f] * da[k], da[k], n2[k]);
       }
-      float h[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) h[k] = 2.f * (k < 2 ? Q[1][1] : Q[2][2]) * n2[k];
-      atomicAdd(c.hacc + kd, h[0]);
-      atomicAdd(c.hacc + c.Kd + kt, h[1]);
-      atomicAdd(c.hacc + c.Kd + c.KT + ks, h[2]);
+      h0 = 2.f * Q[1][1] * n2[0];
+      h1 = 2.f * Q[1][1] * n2[1];
+      h2 = 2.f * Q[2][2] * n2[2];
     }
+    } while (0);
+    const int j1 = kt < 0 ? -1 : c.Kd + kt, j2 = ks < 0 ? -1 : c.Kd + c.KT + ks;
+    warp_run_accum3(gwv, kd, gbd, j1, gtd, j2, gbs, sh.stage[warp]);
+    if (WANT_H) warp_run_accum3(hwv, kd, h0, j1, h1, j2, h2, sh.stage[warp]);
   }
+  partials_reduce<NT>(c, WANT_H);
   return block_sum<NT>((double)acc, sh.red);
 }
 
@@ -490,12 +570,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 // Returns chi2 (sum of residual norms) and, through dnd, sum d^T N d.
 template <int NT, int NOISE, bool GRAD, bool WANT_H>
 __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_out) {
-  if (GRAD || WANT_H) {
-    for (int i = threadIdx.x; i < c.P; i += NT) {
-      if (GRAD) c.gacc[i] = 0.f;
-      if (WANT_H) c.hacc[i] = 0.f;
-    }
-  }
+  if (GRAD || WANT_H) partials_zero<NT>(c, WANT_H);
   fill_tables<NT>(a, c, c.x, c.tab);
   float nb[NB];
 #pragma unroll
@@ -504,7 +579,9 @@ __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_
   const int* ld = c.lab;
   const int* lt = c.lab + c.npix;
   const int* ls = c.lab + 2 * c.npix;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* gwv = c.gw + (long long)warp * c.P;
+  float* hwv = c.hw + (long long)warp * c.P;
   // warp-uniform trip count: every lane reaches the warp-wide gradient scatter
   for (int base = threadIdx.x & ~31; base < c.npix; base += NT) {
     const int p = base + lane;
@@ -548,11 +625,11 @@ __device__ double eval_stream(const FitArgs& a, Ctx& c, Shared& sh, double& dnd_
         }
       }
     }
-    if (GRAD)
-      warp_run_add3(c.gacc, kd, o.gbd, c.gacc + c.Kd, kt, o.gtd, c.gacc + c.Kd + c.KT, ks, o.gbs);
-    if (WANT_H)
-      warp_run_add3(c.hacc, kd, o.hbd, c.hacc + c.Kd, kt, o.htd, c.hacc + c.Kd + c.KT, ks, o.hbs);
+    const int j1 = kt < 0 ? -1 : c.Kd + kt, j2 = ks < 0 ? -1 : c.Kd + c.KT + ks;
+    if (GRAD) warp_run_accum3(gwv, kd, o.gbd, j1, o.gtd, j2, o.gbs, sh.stage[warp]);
+    if (WANT_H) warp_run_accum3(hwv, kd, o.hbd, j1, o.htd, j2, o.hbs, sh.stage[warp]);
   }
+  if (GRAD || WANT_H) partials_reduce<NT>(c, WANT_H);
   block_sum2<NT>(chi, dn, sh.red);
   dnd_out = dn;
   return chi;
@@ -601,49 +678,95 @@ __device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem) {
   return build_moments<NT, NOISE == CSX_NOISE_SEPARABLE>(a, c, smem, sh);
 }
 
+// Collective steps of the L-BFGS driver. The optimiser's vector algebra runs on one leader warp
+// (warp 0), with warp-shuffle reductions and no block barrier; the other warps only take part in
+// the steps that need the whole CTA -- likelihood evaluations, moment builds, finite-difference
+// gradients -- which the leader requests through shared memory (fit_cmd).
+enum FitCmd { CMD_DONE = 0, CMD_EVAL, CMD_EVAL_H, CMD_RECENTRE, CMD_FD_Z, CMD_FD_ZT };
+
+template <int NT, int PATH, int GMODE, int NOISE>
+__device__ double run_cmd(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int cmd, double& dnd) {
+  switch (cmd) {
+    case CMD_EVAL: return objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
+    case CMD_EVAL_H: return objective<NT, PATH, GMODE, NOISE, true>(a, c, sh, dnd);
+    case CMD_RECENTRE: return PATH == CSX_PATH_MOMENT ? recentre<NT, NOISE>(a, c, sh, smem) : 0.0;
+    case CMD_FD_Z:
+      if (GMODE == CSX_GRAD_FD) fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
+      return 0.0;
+    case CMD_FD_ZT:
+      if (GMODE == CSX_GRAD_FD) fd_gradient<NT, NOISE>(a, c, sh, c.zt, c.gt);
+      return 0.0;
+    default: return 0.0;
+  }
+}
+
+// Leader side: publish the command, meet the helpers at a barrier, run the step with them. The
+// leader's earlier writes (c.x) are visible to every thread after the barrier.
+template <int NT, int PATH, int GMODE, int NOISE>
+__device__ double fit_cmd(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int cmd, double& dnd) {
+  if (threadIdx.x == 0) sh.cmd = cmd;
+  __syncthreads();
+  return run_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, cmd, dnd);
+}
+
+template <int NT, int PATH, int GMODE, int NOISE>
+__device__ void fit_helper(const FitArgs& a, Ctx& c, Shared& sh, float* smem) {
+  double dnd = 0.0;
+  for (;;) {
+    __syncthreads();  // the leader's fit_cmd
+    const int cmd = sh.cmd;
+    if (cmd == CMD_DONE) break;
+    (void)run_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, cmd, dnd);
+  }
+}
+
 template <int NT, int PATH, int GMODE, int NOISE>
 __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int q,
                             long long poff) {
+  if (threadIdx.x >= 32) {
+    fit_helper<NT, PATH, GMODE, NOISE>(a, c, sh, smem);
+    return;
+  }
   const int P = c.P;
-  const int tid = threadIdx.x;
+  const int ln = threadIdx.x;  // lane of the leader warp
   const int m = a.history;
+  auto cmd = [&](int k, double& dn) { return fit_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, k, dn); };
   // start point, clamped into the box
-  for (int i = tid; i < P; i += NT) {
+  for (int i = ln; i < P; i += 32) {
     const int t = ptype(c, i);
     c.x[i] = fminf(fmaxf(a.beta0[poff + i], a.lower[t]), a.upper[t]);
   }
-  __syncthreads();
   double dnd = 0.0;
   int recentres = 0;
-  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem);
-  double f = objective<NT, PATH, GMODE, NOISE, true>(a, c, sh, dnd);
+  if (PATH == CSX_PATH_MOMENT) dnd = cmd(CMD_RECENTRE, dnd);
+  double f = cmd(CMD_EVAL_H, dnd);
   int nev = 1;  // likelihood evaluations (each forward pass of a finite difference counts once)
   int status = CSX_FIT_MAXITER, it = 0;
   if (!isfinite(f)) {
-    for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.x[i];
-    if (tid == 0) {
+    for (int i = ln; i < P; i += 32) a.beta_out[poff + i] = c.x[i];
+    if (ln == 0) {
       a.L_out[q] = (double)nan_f();
       a.status[q] = CSX_FIT_NONPHYSICAL;
       a.iters[q] = 0;
       if (a.nevals) a.nevals[q] = nev;
     }
-    __syncthreads();
+    (void)cmd(CMD_DONE, dnd);
     return;
   }
   // scaling by sqrt of the Gauss-Newton diagonal
   float hm = 0.f;
-  for (int i = tid; i < P; i += NT) hm = fmaxf(hm, isfinite(c.hacc[i]) ? c.hacc[i] : 0.f);
-  hm = block_max<NT>(hm, reinterpret_cast<float*>(sh.red));
+  for (int i = ln; i < P; i += 32) hm = fmaxf(hm, isfinite(c.hacc[i]) ? c.hacc[i] : 0.f);
+  hm = warp_max(hm);
   const float hfloor = fmaxf(1e-12f * hm, 1e-30f);
-  for (int i = tid; i < P; i += NT) {
+  for (int i = ln; i < P; i += 32) {
     const float h = c.hacc[i];
     c.hs[i] = sqrtf((isfinite(h) && h > hfloor) ? h : hfloor);
     c.z[i] = c.hs[i] * c.x[i];
     if (GMODE == CSX_GRAD_ADJOINT) c.g[i] = c.gacc[i] / c.hs[i];
   }
-  __syncthreads();
+  __syncwarp();
   if (GMODE == CSX_GRAD_FD) {
-    fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
+    (void)cmd(CMD_FD_Z, dnd);
     nev += 2 * P;
   }
 
@@ -653,40 +776,44 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
   const double delta = 0.1, sigma = 0.9;
   for (it = 0; it < a.max_iter; ++it) {
     // ---- direction: two-loop recursion on the free-set gradient --------------------------
-    for (int i = tid; i < P; i += NT) {
+    for (int i = ln; i < P; i += 32) {
       const int t = ptype(c, i);
       const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
       const float gi = c.g[i];
       const bool act = (c.z[i] <= zl && gi > 0.f) || (c.z[i] >= zu && gi < 0.f);
       c.p[i] = act ? 0.f : gi;
     }
+    __syncwarp();
     for (int j = 0; j < count; ++j) {
       const int k = (head - 1 - j + m) % m;
       const float* Sk = c.S + (long long)k * a.Pmax;
-      float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
-      for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
-      const double dot = block_sum<NT>((double)dotf, sh.red);
+      float dotf = 0.f;  // per-lane partial in FP32, FP64 across the warp
+      for (int i = ln; i < P; i += 32) dotf = fmaf(Sk[i], c.p[i], dotf);
+      const double dot = warp_sum((double)dotf);
       const double al = sh.rho[k] * dot;
-      if (tid == 0) sh.alpha[k] = al;
+      if (ln == 0) sh.alpha[k] = al;
       const float* Yk = c.Y + (long long)k * a.Pmax;
-      for (int i = tid; i < P; i += NT) c.p[i] -= (float)al * Yk[i];
+      for (int i = ln; i < P; i += 32) c.p[i] -= (float)al * Yk[i];
+      __syncwarp();
     }
-    for (int i = tid; i < P; i += NT) c.p[i] *= (float)gamma;
+    for (int i = ln; i < P; i += 32) c.p[i] *= (float)gamma;
+    __syncwarp();
     for (int j = count - 1; j >= 0; --j) {
       const int k = (head - 1 - j + m) % m;
       const float* Yk = c.Y + (long long)k * a.Pmax;
       float dotf = 0.f;
-      for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
-      const double dot = block_sum<NT>((double)dotf, sh.red);
+      for (int i = ln; i < P; i += 32) dotf = fmaf(Yk[i], c.p[i], dotf);
+      const double dot = warp_sum((double)dotf);
       const double be = sh.rho[k] * dot;
       const float* Sk = c.S + (long long)k * a.Pmax;
       const float coef = (float)(sh.alpha[k] - be);
-      for (int i = tid; i < P; i += NT) c.p[i] += coef * Sk[i];
+      for (int i = ln; i < P; i += 32) c.p[i] += coef * Sk[i];
+      __syncwarp();
     }
     // negate, mask the active set and outward steps at a bound, directional derivative, QN step
     float gpf = 0.f;
     float stepn = 0.f;
-    for (int i = tid; i < P; i += NT) {
+    for (int i = ln; i < P; i += 32) {
       const int t = ptype(c, i);
       const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
       const float gi = c.g[i];
@@ -697,15 +824,15 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       gpf = fmaf(gi, pi, gpf);
       stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
     }
-    double gp = block_sum<NT>((double)gpf, sh.red);
-    stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
+    double gp = warp_sum((double)gpf);
+    stepn = warp_max(stepn);
     if (!(gp < 0.0)) {
       // not a descent direction: restart from the projected steepest descent
       count = 0;
       gamma = 1.0;
       gpf = 0.f;
       stepn = 0.f;
-      for (int i = tid; i < P; i += NT) {
+      for (int i = ln; i < P; i += 32) {
         const int t = ptype(c, i);
         const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
         const float gi = c.g[i];
@@ -716,38 +843,36 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         gpf = fmaf(gi, pi, gpf);
         stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
       }
-      gp = block_sum<NT>((double)gpf, sh.red);
-      stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
+      gp = warp_sum((double)gpf);
+      stepn = warp_max(stepn);
       if (!(gp < 0.0)) {
         status = CSX_FIT_CONVERGED;  // projected gradient vanishes
         break;
       }
     }
+    __syncwarp();
     const bool near_opt = CSX_FIT_NEAR > 0.f && recentres == 0 && stepn <= CSX_FIT_NEAR &&
                           last_step <= CSX_FIT_NEAR;
     const bool at_opt = recentres < 6 && stepn <= 1.f && last_step <= 1.f;
     if (PATH == CSX_PATH_MOMENT && it > 0 && (near_opt || at_opt)) {
-      {
-        // The moment form rounds in proportion to the distance from the reference point: at
-        // convergence (and, with CSX_FIT_NEAR > 0, also once the steps first fall within that many
-        // tolerances), move the reference here unless it is already close, so that the last
-        // iterations run on precise values. Each move costs one pass over the pixels.
-        float dref = 0.f;
-        for (int i = tid; i < P; i += NT)
-          dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
-        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
-        if (dref > 30.f) {
-          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
-          __syncthreads();
-          dnd = recentre<NT, NOISE>(a, c, sh, smem);
-          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
-          ++nev;
-          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
-          ++recentres;
-          --it;  // a move of the reference point is not a quasi-Newton iteration
-          __syncthreads();
-          continue;
-        }
+      // The moment form rounds in proportion to the distance from the reference point: at
+      // convergence (and, with CSX_FIT_NEAR > 0, also once the steps first fall within that many
+      // tolerances), move the reference here unless it is already close, so that the last
+      // iterations run on precise values. Each move costs one pass over the pixels.
+      float dref = 0.f;
+      for (int i = ln; i < P; i += 32)
+        dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
+      dref = warp_max(dref);
+      if (dref > 30.f) {
+        for (int i = ln; i < P; i += 32) c.x[i] = c.z[i] / c.hs[i];
+        dnd = cmd(CMD_RECENTRE, dnd);
+        f = cmd(CMD_EVAL, dnd);
+        ++nev;
+        for (int i = ln; i < P; i += 32) c.g[i] = c.gacc[i] / c.hs[i];
+        __syncwarp();
+        ++recentres;
+        --it;  // a move of the reference point is not a quasi-Newton iteration
+        continue;
       }
     }
     if (it > 0 && stepn <= 1.f && last_step <= 1.f) {
@@ -756,13 +881,13 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     }
     // ---- largest step inside the box --------------------------------------------------
     float amax = 1e30f;
-    for (int i = tid; i < P; i += NT) {
+    for (int i = ln; i < P; i += 32) {
       const int t = ptype(c, i);
       const float pi = c.p[i];
       if (pi < 0.f) amax = fminf(amax, (c.hs[i] * a.lower[t] - c.z[i]) / pi);
       else if (pi > 0.f) amax = fminf(amax, (c.hs[i] * a.upper[t] - c.z[i]) / pi);
     }
-    amax = fmaxf(block_min<NT>(amax, reinterpret_cast<float*>(sh.red)), 0.f);
+    amax = fmaxf(warp_min(amax), 0.f);
     // ---- line search (approximate Wolfe) ------------------------------------------------
     const double eps_f = 1e-6 * fabs(f);
     double alpha = fmin(1.0, (double)amax);
@@ -770,25 +895,26 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     double ft = 0.0, dnd_t = 0.0;
     bool ok = false;
     for (int ls = 0; ls < a.max_ls && alpha > 0.0; ++ls) {
-      for (int i = tid; i < P; i += NT) {
+      for (int i = ln; i < P; i += 32) {
         const int t = ptype(c, i);
         const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
         const float zi = fminf(fmaxf(c.z[i] + (float)alpha * c.p[i], zl), zu);
         c.zt[i] = zi;
         c.x[i] = zi / c.hs[i];
       }
-      __syncthreads();
-      ft = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd_t);
+      dnd_t = dnd;
+      ft = cmd(CMD_EVAL, dnd_t);
       ++nev;
       if (GMODE == CSX_GRAD_FD) {
-        fd_gradient<NT, NOISE>(a, c, sh, c.zt, c.gt);
+        (void)cmd(CMD_FD_ZT, dnd_t);
         nev += 2 * P;
       } else {
-        for (int i = tid; i < P; i += NT) c.gt[i] = c.gacc[i] / c.hs[i];
+        for (int i = ln; i < P; i += 32) c.gt[i] = c.gacc[i] / c.hs[i];
       }
+      __syncwarp();
       float dphif = 0.f;
-      for (int i = tid; i < P; i += NT) dphif = fmaf(c.gt[i], c.p[i], dphif);
-      const double dphi = block_sum<NT>((double)dphif, sh.red);
+      for (int i = ln; i < P; i += 32) dphif = fmaf(c.gt[i], c.p[i], dphif);
+      const double dphi = warp_sum((double)dphif);
       if (!isfinite(ft) || !isfinite(dphi)) {
         a_hi = alpha;
         d_hi = 1.0;
@@ -825,19 +951,18 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         // Far from the reference point the moment form's rounding can hide the decrease the
         // line search looks for: move the reference here and try again.
         float dref = 0.f;
-        for (int i = tid; i < P; i += NT)
+        for (int i = ln; i < P; i += 32)
           dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
-        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+        dref = warp_max(dref);
         if (dref > 1.f) {
-          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
-          __syncthreads();
-          dnd = recentre<NT, NOISE>(a, c, sh, smem);
-          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
+          for (int i = ln; i < P; i += 32) c.x[i] = c.z[i] / c.hs[i];
+          dnd = cmd(CMD_RECENTRE, dnd);
+          f = cmd(CMD_EVAL, dnd);
           ++nev;
-          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
+          for (int i = ln; i < P; i += 32) c.g[i] = c.gacc[i] / c.hs[i];
+          __syncwarp();
           ++recentres;
           --it;
-          __syncthreads();
           continue;
         }
       }
@@ -854,7 +979,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     float sn = 0.f;
     float* Sn = c.S + (long long)head * a.Pmax;
     float* Yn = c.Y + (long long)head * a.Pmax;
-    for (int i = tid; i < P; i += NT) {
+    for (int i = ln; i < P; i += 32) {
       const int t = ptype(c, i);
       const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
       Sn[i] = si;
@@ -865,28 +990,27 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       c.z[i] = c.zt[i];
       c.g[i] = c.gt[i];
     }
-    double sy = syf, yy = yyf;
-    block_sum2<NT>(sy, yy, sh.red);
-    sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
+    const double sy = warp_sum((double)syf), yy = warp_sum((double)yyf);
+    sn = warp_max(sn);
     last_step = sn;
     f = ft;
     if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
     if (sy > 1e-12 * yy && yy > 0.0) {
-      if (tid == 0) sh.rho[head] = 1.0 / sy;
+      if (ln == 0) sh.rho[head] = 1.0 / sy;
       head = (head + 1) % m;
       count = min(count + 1, m);
       gamma = sy / yy;
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.z[i] / c.hs[i];
-  if (tid == 0) {
+  for (int i = ln; i < P; i += 32) a.beta_out[poff + i] = c.z[i] / c.hs[i];
+  if (ln == 0) {
     a.L_out[q] = f - dnd;  // L = chi2_min - sum d^T N d
     a.status[q] = status;
     a.iters[q] = it;
     if (a.nevals) a.nevals[q] = nev;
   }
-  __syncthreads();
+  (void)cmd(CMD_DONE, dnd);
 }
 
 // ------------------------------------------------------------------------- AdaTopK --------------
@@ -1193,6 +1317,46 @@ __device__ void fit_problem_adatopk(const FitArgs& a, Ctx& c, Shared& sh, float*
   __syncthreads();
 }
 
+// The problem's view of its CTA slot (layout sized by fit_slot_floats): optimiser vectors, L-BFGS
+// history, SED tables of the current and reference points, warp partials, cell moments.
+template <int NT, int PATH>
+__device__ __forceinline__ void setup_ctx(const FitArgs& a, const ProbDesc& pd, float* base,
+                                          Shared& sh, float* build_smem, Ctx& c) {
+  const long long Pm = a.Pmax;
+  c.P = pd.P;
+  c.Kd = pd.Kd;
+  c.KT = pd.KT;
+  c.Ks = pd.Ks;
+  c.rows = pd.Kd + 2 * pd.KT + pd.Ks;
+  c.npix = a.npix;
+  c.lab = a.labels + (long long)pd.conf * 3 * a.npix;
+  c.perm = a.perm ? a.perm + (long long)pd.conf * a.npix : nullptr;
+  c.coff = a.cell_off ? a.cell_off + (long long)pd.conf * (a.npix + 1) : nullptr;
+  c.ncell = a.ncell ? a.ncell[pd.conf] : 0;
+  c.d = a.d + (long long)pd.real * a.npix * 2 * NB;
+  c.z = base;
+  c.g = base + Pm;
+  c.p = base + 2 * Pm;
+  c.zt = base + 3 * Pm;
+  c.gt = base + 4 * Pm;
+  c.hs = base + 5 * Pm;
+  c.x = base + 6 * Pm;
+  const bool sm = pd.P <= SMEM_P;
+  c.gacc = sm ? sh.gacc : base + 7 * Pm;
+  c.hacc = sm ? sh.hacc : base + 8 * Pm;
+  c.S = base + 9 * Pm;
+  c.Y = c.S + (long long)a.history * Pm;
+  c.tab = c.Y + (long long)a.history * Pm;
+  c.tabr = c.tab + (long long)a.rows_max * NB;
+  c.xr = c.tabr + (long long)a.rows_max * NB;
+  float* gwg = c.xr + Pm;  // warp partials in global memory: [8][Pmax] gradient, then GN diagonal
+  c.gw = sm ? build_smem + fit_rows_floats<NT, PATH>() : gwg;
+  c.hw = gwg + 8 * Pm;
+  c.mom = gwg + 16 * Pm;
+  c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * a.ncell_max);
+  c.smem = build_smem;
+}
+
 template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>
 __global__ void __launch_bounds__(NT, (PATH == CSX_PATH_MOMENT && NT <= 128)
                                          ? CSX_FIT_MIN_BLOCKS * (128 / NT) : 1)
@@ -1202,7 +1366,6 @@ k_fit(const __grid_constant__ FitArgs a) {
   extern __shared__ float4 build_smem4[];  // moment build staging (moment path only)
   float* build_smem = reinterpret_cast<float*>(build_smem4);
   float* base = a.slots + (long long)blockIdx.x * a.slot_floats;
-  const int Pm = a.Pmax;
   for (;;) {
     if (threadIdx.x == 0) s_q = atomicAdd(a.head, 1);
     __syncthreads();
@@ -1212,35 +1375,22 @@ k_fit(const __grid_constant__ FitArgs a) {
     const int q = a.order[qi];
     const ProbDesc pd = a.probs[q];
     Ctx c;
-    c.P = pd.P;
-    c.Kd = pd.Kd;
-    c.KT = pd.KT;
-    c.Ks = pd.Ks;
-    c.rows = pd.Kd + 2 * pd.KT + pd.Ks;
-    c.npix = a.npix;
-    c.lab = a.labels + (long long)pd.conf * 3 * a.npix;
-    c.perm = a.perm ? a.perm + (long long)pd.conf * a.npix : nullptr;
-    c.coff = a.cell_off ? a.cell_off + (long long)pd.conf * (a.npix + 1) : nullptr;
-    c.ncell = a.ncell ? a.ncell[pd.conf] : 0;
-    c.d = a.d + (long long)pd.real * a.npix * 2 * NB;
-    c.z = base;
-    c.g = base + Pm;
-    c.p = base + 2 * Pm;
-    c.zt = base + 3 * Pm;
-    c.gt = base + 4 * Pm;
-    c.hs = base + 5 * Pm;
-    c.x = base + 6 * Pm;
-    const bool sm = pd.P <= SMEM_P;
-    c.gacc = sm ? sh.gacc : base + 7 * Pm;
-    c.hacc = sm ? sh.hacc : base + 8 * Pm;
-    c.S = base + 9 * Pm;
-    c.Y = c.S + (long long)a.history * Pm;
-    c.tab = c.Y + (long long)a.history * Pm;
-    c.tabr = c.tab + (long long)a.rows_max * NB;
-    c.xr = c.tabr + (long long)a.rows_max * NB;
-    c.mom = c.xr + Pm;
-    c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * a.ncell_max);
-    c.smem = build_smem;
+    setup_ctx<NT, PATH>(a, pd, base, sh, build_smem, c);
+    if (PATH == CSX_PATH_MOMENT && c.ncell < 0) {
+      // the configuration has a label outside [0, K_j) (found when its cells were built)
+      for (int i = threadIdx.x; i < c.P; i += NT) {
+        const int t = ptype(c, i);
+        a.beta_out[pd.poff + i] = fminf(fmaxf(a.beta0[pd.poff + i], a.lower[t]), a.upper[t]);
+      }
+      if (threadIdx.x == 0) {
+        a.L_out[q] = (double)nan_f();
+        a.status[q] = CSX_FIT_BADLABEL;
+        a.iters[q] = 0;
+        if (a.nevals) a.nevals[q] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
     if (SOLVER == CSX_SOLVER_ADATOPK)
       fit_problem_adatopk<NT, PATH, NOISE>(a, c, sh, build_smem, q, pd.poff);
     else
@@ -1252,6 +1402,7 @@ k_fit(const __grid_constant__ FitArgs a) {
 int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path, long long* out) {
   long long n = (long long)(9 + 2 * history) * Pmax + (long long)rows_max * NB;
   n += (long long)rows_max * NB + Pmax;  // reference tables and parameters (moment path)
+  n += 16LL * Pmax;                      // warp partials (gradient, Gauss-Newton diagonal)
   if (path == CSX_PATH_MOMENT) n += (long long)NM * ncell_max + 3LL * ncell_max;
   n = (n + 63) & ~63LL;
   *out = n;
@@ -1260,10 +1411,60 @@ int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path
 
 template <int NT, int PATH>
 constexpr size_t fit_dyn_smem() {
-  // build staging (32 pixel rows per warp) or, during evaluations, 30 + 171 floats per thread
+  // moment path: build staging (32 pixel rows per warp) or, during evaluations, 30 (+ 171) floats
+  // per thread followed by the warp partials; streaming path: the warp partials
   constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
-  constexpr size_t rows = (size_t)(30 + (CSX_FIT_STAGE_MOMENTS ? NM : 0)) * NT;
-  return PATH == CSX_PATH_MOMENT ? (build > rows ? build : rows) * sizeof(float) : 0;
+  constexpr size_t eval = (size_t)fit_rows_floats<NT, PATH>() + (size_t)(NT / 32) * SMEM_P;
+  if (PATH != CSX_PATH_MOMENT) return eval * sizeof(float);
+  return (build > eval ? build : eval) * sizeof(float);
+}
+
+// ------------------------------------------------------------------ fixed-point evaluation ------
+// L and dL/dbeta of nprob problems of one configuration by the fit's own cell-moment evaluation:
+// per problem q (realization q), the residual moments of its cells about beta0[q] (one pass over
+// the pixels, build_moments), then L = chi2 - sum d^T N d and the gradient at beta_eval[q] from the
+// moments alone (eval_moment). CTA b takes problems b, b + grid, ...; slot layout as the fit's.
+template <int NT, int NOISE>
+__global__ void __launch_bounds__(NT, CSX_FIT_MIN_BLOCKS) k_cell_eval(const __grid_constant__ FitArgs a) {
+  __shared__ Shared sh;
+  extern __shared__ float4 ce_smem4[];
+  float* build_smem = reinterpret_cast<float*>(ce_smem4);
+  float* base = a.slots + (long long)blockIdx.x * a.slot_floats;
+  for (int q = blockIdx.x; q < a.nprob; q += gridDim.x) {
+    const ProbDesc pd = a.probs[q];
+    Ctx c;
+    setup_ctx<NT, CSX_PATH_MOMENT>(a, pd, base, sh, build_smem, c);
+    if (c.ncell < 0) {  // a label outside [0, K_j)
+      for (int i = threadIdx.x; i < c.P; i += NT) a.grad_out[pd.poff + i] = nan_f();
+      if (threadIdx.x == 0) a.L_out[q] = (double)nan_f();
+      continue;
+    }
+    for (int i = threadIdx.x; i < c.P; i += NT) c.x[i] = a.beta0[pd.poff + i];
+    __syncthreads();
+    const double dnd = recentre<NT, NOISE>(a, c, sh, build_smem);
+    for (int i = threadIdx.x; i < c.P; i += NT) c.x[i] = a.beta_eval[pd.poff + i];
+    __syncthreads();
+    const double chi = eval_moment<NT, false>(a, c, sh);
+    for (int i = threadIdx.x; i < c.P; i += NT) a.grad_out[pd.poff + i] = c.gacc[i];
+    if (threadIdx.x == 0) a.L_out[q] = chi - dnd;
+    __syncthreads();
+  }
+}
+
+template <int NOISE>
+static int launch_cell_eval_t(const FitArgs& a, int grid, cudaStream_t s) {
+  constexpr size_t dyn = fit_dyn_smem<128, CSX_PATH_MOMENT>();
+  CSX_CUDA(cudaFuncSetAttribute(k_cell_eval<128, NOISE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dyn));
+  k_cell_eval<128, NOISE><<<grid, 128, dyn, s>>>(a);
+  CSX_CUDA(cudaGetLastError());
+  return CSX_OK;
+}
+
+int launch_cell_eval(const FitArgs& a, int grid, cudaStream_t s) {
+  if (a.nprob == 0) return CSX_OK;
+  return a.noise_kind == CSX_NOISE_SEPARABLE ? launch_cell_eval_t<CSX_NOISE_SEPARABLE>(a, grid, s)
+                                             : launch_cell_eval_t<CSX_NOISE_HOMOGENEOUS>(a, grid, s);
 }
 
 template <int NT, int PATH, int GMODE, int NOISE, int SOLVER>

@@ -5,6 +5,22 @@
 
 namespace csx {
 
+// Count of bounded waits that gave up (a tensor copy that did not arrive within the bound) since the
+// last device_timeouts() on this device; the affected problem's L is also set to NaN.
+__device__ unsigned int g_wait_timeouts;
+
+int device_timeouts(cudaStream_t s, unsigned* count) {
+  CSX_CUDA(cudaStreamSynchronize(s));
+  unsigned v = 0;
+  CSX_CUDA(cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)));
+  if (v) {
+    const unsigned zero = 0;
+    CSX_CUDA(cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero)));
+  }
+  *count = v;
+  return CSX_OK;
+}
+
 // One thread per (problem, row, band) table entry.
 __global__ void k_tables(Bands b, int nprob, int Kd, int KT, int Ks, const float* __restrict__ beta,
                          float* __restrict__ tables) {
@@ -377,6 +393,7 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
       for (int jj = j; jj < my && jj < j + TS_S; ++jj)
         (void)mbar_wait_bounded(&full[jj % TS_S], (unsigned)(jj / TS_S) & 1u, TS_WAIT_CYCLES);
       atomicAdd(a.L + q, (double)nan_f());
+      atomicAdd(&g_wait_timeouts, 1u);
     }
     return;
   }

@@ -19,13 +19,16 @@ NOISE = {"homogeneous": 0, "separable": 1, "perpixel": 2}
 PATH = {"auto": 0, "stream": 1, "moment": 2}
 GRAD = {"adjoint": 0, "fd": 1}
 SOLVER = {"lbfgs": 0, "adatopk": 1}
-STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search"}
+STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search", 4: "bad_label"}
 M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
-EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_fit_defaults", "csx_mixing",
-           "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_noalloc",
-           "csx_build_cells", "csx_fit_batch", "csx_reconstruct", "csx_select", "csx_kmeans",
-           "csx_sht_plan_create", "csx_sht_plan_destroy", "csx_pseudo_cl", "csx_residual_cl"]
+EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_device_status",
+           "csx_fit_defaults", "csx_mixing",
+           "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_f64",
+           "csx_spectral_grad_noalloc",
+           "csx_cell_like_grad", "csx_build_cells", "csx_fit_batch", "csx_reconstruct",
+           "csx_select", "csx_kmeans", "csx_sht_plan_create", "csx_sht_plan_destroy",
+           "csx_pseudo_cl", "csx_residual_cl"]
 
 
 class CsxError(RuntimeError):
@@ -66,12 +69,17 @@ def lib():
         L.csx_version.restype = ctypes.c_char_p
         L.csx_last_error.restype = ctypes.c_char_p
         L.csx_release.restype = i32
+        L.csx_device_status.argtypes = [vp]
         L.csx_fit_defaults.argtypes = [POINTER(CFitOpts)]
         L.csx_mixing.argtypes = [POINTER(CModel), i32, vp, vp, vp, vp]
         L.csx_spectral_like.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp]
         L.csx_spectral_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp, vp]
+        L.csx_spectral_grad_f64.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp,
+                                            vp, vp]
         L.csx_spectral_grad_noalloc.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp,
                                                 vp, vp, vp]
+        L.csx_cell_like_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp,
+                                         vp, vp, vp]
         L.csx_build_cells.argtypes = [i32, i32, vp, pi32, vp, vp, vp, vp]
         L.csx_fit_batch.argtypes = [POINTER(CModel), POINTER(CSky), i32, vp, pi32,
                                     POINTER(CFitOpts), vp, vp, vp, vp, vp, vp, vp]
@@ -178,6 +186,12 @@ def release():
     _check(lib().csx_release())
 
 
+def device_status():
+    """Raise CsxError (CSX_ETIMEOUT) if a bounded device wait gave up since the last check;
+    synchronises torch's current stream."""
+    _check(lib().csx_device_status(_stream()))
+
+
 def mixing(model: Model, beta: torch.Tensor, want_derivatives=True):
     """A [n, 16, 3] and dA [n, 3, 16] for beta [n, 3] = (beta_d, T_d, beta_s)."""
     beta = beta.to(torch.float32).contiguous()
@@ -209,16 +223,63 @@ def spectral_grad(model: Model, sky: Sky, labels, K, beta):
     return L, g
 
 
-def spectral_grad_noalloc(model: Model, sky: Sky, labels, K, beta, L, grad):
-    """csx_spectral_grad_noalloc into caller-provided outputs L [nprob] float64 and grad [nprob, P]
-    float32: the library allocates no device memory for this call (for callers whose device memory
-    is owned by their own allocator or budget)."""
+def spectral_grad_f64(model: Model, sky: Sky, labels, K, beta, want_grad=True):
+    """(L [nprob] float64, grad [nprob, P] float64 or None) with every operation in FP64."""
     K, Kp = _host_i32(K)
-    beta = beta.to(torch.float32).contiguous()
+    beta = beta.to(torch.float64).contiguous()
+    L = torch.empty(beta.shape[0], device=beta.device, dtype=torch.float64)
+    g = torch.empty_like(beta) if want_grad else None
+    _check(lib().csx_spectral_grad_f64(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
+                                       beta.shape[0], _ptr(beta), _ptr(L), _ptr(g), _stream()))
+    return L, g
+
+
+def spectral_grad_noalloc(model: Model, sky: Sky, labels, K, beta, L, grad):
+    """csx_spectral_grad_noalloc into caller-provided outputs: the library allocates no device
+    memory for this call (for callers whose device memory is owned by their own allocator or
+    budget). Every tensor must already have the layout the C entry point reads, on the data's
+    device: beta float32 [nprob, P], L float64 [nprob], grad float32 [nprob, P], labels int32
+    [3, npix], all contiguous; nothing is converted or copied here (a conversion would allocate),
+    and anything else is refused before the call."""
+    K, Kp = _host_i32(K)
+    if K.shape != (3,):
+        raise ValueError("K must hold three patch counts")
+    P = int(K.astype(np.int64).sum())
+    dev = sky.d.device
+    want = (("beta", beta, torch.float32), ("L", L, torch.float64), ("grad", grad, torch.float32),
+            ("labels", labels, torch.int32))
+    for name, t, dt in want:
+        if not isinstance(t, torch.Tensor) or t.device != dev or t.dtype != dt or \
+                not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor on %s" % (name, dt, dev))
+    if beta.dim() != 2 or beta.shape[1] != P:
+        raise ValueError("beta must be [nprob, %d]" % P)
+    nprob = beta.shape[0]
+    if L.shape != (nprob,):
+        raise ValueError("L must be [%d]" % nprob)
+    if grad.shape != (nprob, P):
+        raise ValueError("grad must be [%d, %d]" % (nprob, P))
+    if labels.shape != (3, sky.npix):
+        raise ValueError("labels must be [3, %d]" % sky.npix)
     _check(lib().csx_spectral_grad_noalloc(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels),
-                                           Kp, beta.shape[0], _ptr(beta), _ptr(L), _ptr(grad),
-                                           _stream()))
+                                           Kp, nprob, _ptr(beta), _ptr(L), _ptr(grad), _stream()))
     return L, grad
+
+
+def cell_like_grad(model: Model, sky: Sky, labels, K, beta_ref, beta):
+    """(L [nprob] float64, grad [nprob, P] float32) at beta [nprob, P] by the fit's cell-moment
+    evaluation, the moments formed about beta_ref [nprob, P] (homogeneous or separable noise)."""
+    K, Kp = _host_i32(K)
+    beta_ref = beta_ref.to(torch.float32).contiguous()
+    beta = beta.to(torch.float32).contiguous()
+    if beta.shape != beta_ref.shape:
+        raise ValueError("beta and beta_ref must have the same shape")
+    L = torch.empty(beta.shape[0], device=beta.device, dtype=torch.float64)
+    g = torch.empty_like(beta)
+    _check(lib().csx_cell_like_grad(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
+                                    beta.shape[0], _ptr(beta_ref), _ptr(beta), _ptr(L), _ptr(g),
+                                    _stream()))
+    return L, g
 
 
 def build_cells(labels: torch.Tensor, K):
@@ -414,42 +475,58 @@ def chunk(n: int, world: int, rank: int):
     return (rank * n) // world, ((rank + 1) * n) // world
 
 
-def gather_select(vtot: torch.Tensor, group=None):
-    """Selection across processes: every rank holds V_tot of its own configurations (in rank
-    order of the global numbering); all ranks receive (V_tot of all configurations, global index
-    of the smallest, ties to the lowest index). The only exchange of the path: one all-gather of
-    per-configuration scalars (nccl for device tensors, gloo for host tensors)."""
+def gather_metrics(metrics: torch.Tensor, group=None):
+    """The path's one exchange across processes: every rank holds the metric rows
+    [n_r, CSX_NMETRIC] (float64) of its own problems, numbered in rank order in the global problem
+    list; every rank receives all rows, concatenated in rank order (one all-gather of the sizes,
+    one of the padded rows; nccl for CUDA tensors, gloo for host tensors)."""
     import torch.distributed as dist
+    if metrics.dim() != 2 or metrics.shape[1] != NMETRIC or metrics.dtype != torch.float64:
+        raise ValueError("metrics must be float64 [n, %d]" % NMETRIC)
     world = dist.get_world_size(group)
-    n = torch.tensor([vtot.numel()], dtype=torch.int64, device=vtot.device)
+    n = torch.tensor([metrics.shape[0]], dtype=torch.int64, device=metrics.device)
     sizes = [torch.zeros_like(n) for _ in range(world)]
     dist.all_gather(sizes, n, group=group)
     sizes = [int(x.item()) for x in sizes]
-    m = max(sizes)
-    pad = torch.full((m,), float("inf"), dtype=torch.float64, device=vtot.device)
-    pad[: vtot.numel()] = vtot.to(torch.float64)
+    pad = torch.zeros((max(sizes), NMETRIC), dtype=torch.float64, device=metrics.device)
+    pad[: metrics.shape[0]] = metrics
     parts = [torch.empty_like(pad) for _ in range(world)]
-    dist.all_gather(parts, pad, group=group)
-    allv = torch.cat([p[:k] for p, k in zip(parts, sizes)])
-    # argmin with ties to the lowest index (NaN never wins)
-    key = torch.where(torch.isnan(allv), torch.full_like(allv, float("inf")), allv)
-    best = int(torch.nonzero(key == key.min())[0].item()) if allv.numel() else -1
-    return allv, best
+    dist.all_gather(parts, pad.contiguous(), group=group)
+    return torch.cat([p[:k] for p, k in zip(parts, sizes)]).contiguous()
+
+
+def gather_select(metrics: torch.Tensor, nreal: int, group=None):
+    """Selection across processes: gather_metrics, then csx_select over all configurations (each
+    rank holds whole configurations, nreal problems each) on this rank's device. Returns (V_tot of
+    every configuration [nconf_total] float64, index of the best [1] int32), as csx_select."""
+    allm = gather_metrics(metrics, group)
+    if allm.shape[0] % nreal:
+        raise ValueError("every rank must hold whole configurations")
+    return select(allm, allm.shape[0] // nreal, nreal)
 
 
 class SpectralLikelihood(torch.autograd.Function):
     """L(beta) for one configuration as a differentiable torch op (Sec. 3.3.1).
 
-    forward: csx_spectral_grad (one streaming pass gives L and dL/dbeta); only the gradient
-    [nprob, P] is saved, no per-pixel intermediate. backward: grad_output[:, None] * dL/dbeta."""
+    forward: csx_spectral_grad (one streaming pass gives L and dL/dbeta; FP32 arithmetic with FP64
+    sums) or, with precision="fp64", csx_spectral_grad_f64 (every operation in FP64); only the
+    gradient [nprob, P] is saved, no per-pixel intermediate. backward: grad_output[:, None] *
+    dL/dbeta, in beta's dtype."""
 
     @staticmethod
-    def forward(ctx, beta, model, sky, labels, K):
-        L, g = spectral_grad(model, sky, labels, K, beta.detach())
+    def forward(ctx, beta, model, sky, labels, K, precision="fp32"):
+        if precision == "fp64":
+            L, g = spectral_grad_f64(model, sky, labels, K, beta.detach())
+        elif precision == "fp32":
+            L, g = spectral_grad(model, sky, labels, K, beta.detach())
+        else:
+            raise ValueError("precision must be 'fp32' or 'fp64'")
         ctx.save_for_backward(g)
+        ctx.beta_dtype = beta.dtype
         return L
 
     @staticmethod
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
-        return (grad_out.to(g.dtype)[:, None] * g).to(torch.float32), None, None, None, None
+        gb = grad_out.to(torch.float64)[:, None] * g.to(torch.float64)
+        return gb.to(ctx.beta_dtype), None, None, None, None, None

@@ -13,6 +13,17 @@ def fit_job(args):
     return x, L, info["interior"]
 
 
+def grad_job(args):
+    """(L, dL/dbeta, term scale S, data-scale term scale Sd) of the oracle at one point."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    from oracle import likelihood as lk
+    nu, d64, ninv64, labels, K, beta = args
+    L, g = lk.spectral_gradient(nu, d64, ninv64, labels, K, beta)
+    return (L, g, lk.gradient_term_scale(nu, d64, ninv64, labels, K, beta),
+            lk.gradient_term_scale(nu, d64, ninv64, labels, K, beta, data_scale=True))
+
+
 def oracle_pool(n):
     import multiprocessing as mp
     saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",

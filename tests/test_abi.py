@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "csx.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(csx_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(csx_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -131,3 +131,37 @@ def test_residual_spectra_arguments_are_refused_on_the_host(lib):
     ok = ctypes.c_void_p(0x10000)
     rc = lib.csx_residual_cl(None, 2, ok, 12, 6, 3, None, ok, 1, ok, ok, ok, None)
     assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
+
+
+def test_patch_counts_are_bounded_on_the_host(lib):
+    """K_j above CSX_MAX_K (where sizes such as P = K_d + K_T + K_s would leave 32-bit range) are
+    refused before anything touches a device; so is per-pixel noise for the cell-moment call. The
+    pointers below are never dereferenced."""
+    import ctypes
+    from paper_2604_08463_b300 import csx
+    model = csx.Model(np.array([40.0, 100.0, 402.0]))
+    sky = csx.CSky()
+    sky.npix, sky.nreal, sky.noise_kind = 10, 1, 0
+    for f in range(3):
+        sky.ninv_band[f] = 1.0
+    ok = ctypes.c_void_p(0x10000)
+    sky.d = 0x10000
+    big = (ctypes.c_int32 * 3)(2 ** 31 - 1, 2 ** 30, 2)
+    rc = lib.csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky), ok, big, 1, ok, ok, ok, None)
+    assert rc == -1 and b"K_j" in lib.csx_last_error()
+    rc = lib.csx_spectral_grad_noalloc(ctypes.byref(model.c), ctypes.byref(sky), ok, big, 1, ok, ok,
+                                       ok, None)
+    assert rc == -1 and b"K_j" in lib.csx_last_error()
+    rc = lib.csx_cell_like_grad(ctypes.byref(model.c), ctypes.byref(sky), ok, big, 1, ok, ok, ok,
+                                ok, None)
+    assert rc == -1 and b"K_j" in lib.csx_last_error()
+    opts = csx.fit_options()
+    rc = lib.csx_fit_batch(ctypes.byref(model.c), ctypes.byref(sky), 1, ok, big, ctypes.byref(opts),
+                           ok, ok, ok, ok, ok, None, None)
+    assert rc == -1 and b"K_j" in lib.csx_last_error()
+    small = (ctypes.c_int32 * 3)(2, 2, 2)
+    sky.noise_kind = 2
+    sky.ninv_pix = 0x10000
+    rc = lib.csx_cell_like_grad(ctypes.byref(model.c), ctypes.byref(sky), ok, small, 1, ok, ok, ok,
+                                ok, None)
+    assert rc == -1 and b"homogeneous or separable" in lib.csx_last_error()

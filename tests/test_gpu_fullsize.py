@@ -22,7 +22,7 @@ os.environ.setdefault("CSX_KMEANS_CACHE", os.path.join(ROOT, ".cache", "kmeans")
 
 from synth import workloads  # noqa: E402
 from tests._inputs import Case, pack  # noqa: E402
-from tests._fitcheck import sampled_fit_check as _sampled_fit_check  # noqa: E402
+from tests._fitcheck import sampled_fit_check as _sampled_fit_check, stored_refs  # noqa: E402
 from tests._parity import TOL_BETA, assert_grad_close, grad_ref  # noqa: E402
 
 
@@ -55,6 +55,11 @@ def test_fullsky_nside64_hundred_realizations(csx):
 
 
 def test_gradcheck_nside128_autograd_64_points(csx):
+    """The differentiation check at nside 128 (196608 pixels, K = 256 per parameter, P = 768): the
+    autograd function's gradient in FP32 and in all-FP64 at 64 random points against the FP64
+    oracle at every point, and against central finite differences (step 1e-4) of the all-FP64
+    likelihood on a subset of components. Only the gradient is kept between forward and backward."""
+    from tests._oracle_jobs import grad_job, oracle_pool
     K = (256, 256, 256)
     wl = workloads.gradcheck(128, K, npoints=64)
     case = Case(wl, "separable")
@@ -65,22 +70,66 @@ def test_gradcheck_nside128_autograd_64_points(csx):
                   w=torch.from_numpy(case.w32).to("cuda"))
     model = csx.Model(case.nu)
     labels = torch.from_numpy(np.ascontiguousarray(lab)).to("cuda")
-    bt = torch.tensor(beta, device="cuda", requires_grad=True)
-    L = csx.SpectralLikelihood.apply(bt, model, sky, labels, K)
-    L.sum().backward()
+    out = {}
+    for prec, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+        bt = torch.tensor(beta, device="cuda", dtype=dt, requires_grad=True)
+        L = csx.SpectralLikelihood.apply(bt, model, sky, labels, K, prec)
+        L.sum().backward()
+        torch.cuda.synchronize()
+        assert bt.grad.dtype == dt
+        out[prec] = (L.detach().cpu().numpy(), bt.grad.cpu().numpy().astype(np.float64))
+        assert np.isfinite(out[prec][0]).all() and np.isfinite(out[prec][1]).all()
+    jobs = [(case.nu, case.d64(0), case.ninv64, lab, K, beta[i].astype(np.float64)) for i in range(64)]
+    with oracle_pool(8) as pool:
+        refs = pool.map(grad_job, jobs)
+    worst32 = worst64 = 0.0
+    ratio = 0.0
+    for i, (Lr, gr, Sr, Sdr) in enumerate(refs):
+        L32, g32 = out["fp32"][0][i], out["fp32"][1][i]
+        L64, g64 = out["fp64"][0][i], out["fp64"][1][i]
+        assert abs(L32 - Lr) <= 1e-5 * abs(Lr), (i, L32, Lr)
+        ratio = max(ratio, assert_grad_close(g32, gr, Sr, Sdr)[1])
+        assert abs(L64 - Lr) <= 1e-11 * abs(Lr), (i, L64, Lr)
+        scale = np.abs(gr).max()
+        assert np.abs(g64 - gr).max() <= 1e-9 * scale, (i, np.abs(g64 - gr).max() / scale)
+        assert np.all(np.abs(g64 - gr) <= 1e-9 * np.abs(gr) + 1e-12 * Sr), i
+        worst32 = max(worst32, np.abs(g32 - gr).max() / scale)
+        worst64 = max(worst64, np.abs(g64 - gr).max() / scale)
+    print("max-norm relative gradient error vs the oracle: FP32 %.2e, FP64 %.2e; largest FP32 "
+          "component error / its bound %.3f" % (worst32, worst64, ratio))
+    # central differences (h = 1e-4) of the all-FP64 likelihood at 4 points, 6 components each
+    # (two per parameter type), all perturbed points in one call
+    P = sum(K)
+    comps = [0, 137, 256, 400, 512, 700]
+    rows, where = [], []
+    for i in (0, 21, 42, 63):
+        for j in comps:
+            for sgn in (1.0, -1.0):
+                b = beta[i].astype(np.float64).copy()
+                b[j] += sgn * 1e-4
+                rows.append(b)
+            where.append((i, j))
+    d2 = torch.from_numpy(case.d32).to("cuda").repeat(len(rows), 1, 1, 1)
+    sky2 = csx.Sky(d2, noise="separable", ninv_band=case.nb32,
+                   w=torch.from_numpy(case.w32).to("cuda"))
+    Lfd, _ = csx.spectral_grad_f64(model, sky2, labels, K, torch.tensor(np.array(rows), device="cuda"),
+                                   want_grad=False)
     torch.cuda.synchronize()
-    Lg, g = L.detach().cpu().numpy(), bt.grad.cpu().numpy()
-    assert np.isfinite(Lg).all() and np.isfinite(g).all()
-    for i in (0, 9, 31, 63):
-        Lr, gr, Sr = grad_ref(case, 0, lab, K, beta[i].astype(np.float64))
-        assert abs(Lg[i] - Lr) <= 1e-5 * abs(Lr), (i, Lg[i], Lr)
-        assert_grad_close(g[i], gr, Sr)
+    Lfd = Lfd.cpu().numpy()
+    for k, (i, j) in enumerate(where):
+        fd = (Lfd[2 * k] - Lfd[2 * k + 1]) / 2e-4
+        g64, g32 = out["fp64"][1][i], out["fp32"][1][i]
+        gmax = np.abs(g64).max()
+        assert abs(g64[j] - fd) <= 1e-5 * abs(fd) + 1e-6 * gmax, (i, j, g64[j], fd)
+        assert abs(g32[j] - fd) <= 1e-4 * abs(fd) + 1e-5 * gmax, (i, j, g32[j], fd)
+    del d2, sky2
+    assert P == 768
 
 
 def test_bench_scan_fit_sampled_problems(csx):
     """The bench's workload and launch: every one of the 10000 problems in one persistent launch;
-    six problems (P spread over the scan's lower half, where oracle fits take seconds) are refitted
-    by the oracle."""
+    nine problems spread over the scan's P range (six below 200, three from 600 to 1314) against
+    stored oracle fits (tests/golden/make_fit_refs.py)."""
     wl = workloads.scan(nside=64, nconf=1000, kmax=500, nreal=10, b_cut_deg=20.0, seed=4)
     case = Case(wl, "separable")
     model, sky, labels = case.gpu()
@@ -91,14 +140,9 @@ def test_bench_scan_fit_sampled_problems(csx):
     status = res["status"].cpu().numpy()
     assert (status == 0).mean() >= 0.999, np.bincount(status)
     P = np.repeat(wl.P, wl.nreal)
-    rng = np.random.default_rng(17)
-    picks = []
-    for lo, hi in ((3, 20), (20, 50), (50, 80), (80, 120), (120, 160), (160, 200)):
-        cand = np.nonzero((P >= lo) & (P < hi))[0]
-        picks.append(int(rng.choice(cand)))
-    worst, floored, vfl, unc, jt = _sampled_fit_check(csx, case, res, picks)
-    print("worst |err|/tol %.3f; within the gradient floor: %d; value floor: %d; unconstrained: %d; "
-          "joint: %d" % (worst, floored, vfl, unc, jt))
+    picks, refs = stored_refs("scan64", case)
+    print("sampled problems", picks, "P", P[picks].tolist())
+    _sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=refs)
 
 
 def test_large_k_scan_nside16_sampled_problems(csx):
@@ -112,8 +156,54 @@ def test_large_k_scan_nside16_sampled_problems(csx):
     res = csx.fit_batch(model, sky, labels, wl.K, beta0)
     torch.cuda.synchronize()
     P = np.repeat(wl.P, wl.nreal)
-    order = np.argsort(P)
-    picks = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
-    worst, floored, vfl, unc, jt = _sampled_fit_check(csx, case, res, picks)
-    print("P", P[picks], "worst |err|/tol %.3f; within the gradient floor: %d; value floor: %d; "
-          "unconstrained: %d; joint: %d" % (worst, floored, vfl, unc, jt))
+    picks, refs = stored_refs("scan16_k1000", case)
+    print("P", P[picks])
+    _sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=refs)
+
+
+def test_cell_moment_evaluation_nside64_scan(csx):
+    """The fit's cell-moment evaluation of L and dL/dbeta at fixed points, on configurations of the
+    bench's nside-64 scan (small, median and large P), against the oracle's pixel-by-pixel
+    likelihood: at a point near the moments' reference point (10 tolerances away), at an
+    independent random point, and at a point far from it (uniform inside the box, away from the
+    bounds by 10% of their span), where the residual moments' rounding is largest. Tolerances of
+    the parity tests."""
+    from tests._oracle_jobs import grad_job, oracle_pool
+    wl = workloads.scan(nside=64, nconf=1000, kmax=500, nreal=10, b_cut_deg=20.0, seed=4)
+    case = Case(wl, "separable")
+    model, sky, labels = case.gpu()
+    order = np.argsort(wl.P, kind="stable")
+    confs = [int(order[50]), int(order[len(order) // 2]), int(order[-1])]
+    rng = np.random.default_rng(29)
+    lo, hi = np.array(workloads.LOWER), np.array(workloads.UPPER)
+    jobs, got = [], []
+    for c in confs:
+        K = wl.K[c]
+        P = int(K.sum())
+        types = np.concatenate([np.full(K[j], j) for j in range(3)])
+        ref = workloads.random_points(K, 3, seed=100 + c)
+        pts = np.empty_like(ref)
+        pts[0] = ref[0] + 10 * TOL_BETA[types] * rng.standard_normal(P)
+        pts[1] = workloads.random_points(K, 1, seed=200 + c)[0]
+        span = hi - lo
+        pts[2] = rng.uniform(lo[types] + 0.1 * span[types], hi[types] - 0.1 * span[types])
+        Lg, g = csx.cell_like_grad(model, sky, labels[c], K, torch.tensor(ref, device="cuda"),
+                                   torch.tensor(pts, device="cuda"))
+        torch.cuda.synchronize()
+        got.append((Lg.cpu().numpy(), g.cpu().numpy()))
+        p32 = pts.astype(np.float32).astype(np.float64)
+        for r in range(3):
+            jobs.append((case.nu, case.d64(r), case.ninv64, wl.labels[c], K, p32[r]))
+    with oracle_pool(8) as pool:
+        refs = pool.map(grad_job, jobs)
+    for k, c in enumerate(confs):
+        for r in range(3):
+            Lr, gr, Sr, Sdr = refs[3 * k + r]
+            Lg, g = got[k][0][r], got[k][1][r]
+            print("configuration %d (P %d) point %d: L rel err %.2e, grad max-norm rel err %.2e, "
+                  "largest component error / bound %.3f, / 1e-5 S %.3f"
+                  % (c, wl.P[c], r, abs(Lg - Lr) / abs(Lr), np.abs(g - gr).max() / np.abs(gr).max(),
+                     (np.abs(g - gr) / (1e-4 * np.abs(gr) + np.maximum(1e-5 * Sr, 32 * 2.0 ** -24 * Sdr))).max(),
+                     (np.abs(g - gr) / (1e-4 * np.abs(gr) + 1e-5 * Sr)).max()))
+            assert abs(Lg - Lr) <= 1e-5 * abs(Lr), (c, r, Lg, Lr)
+            assert_grad_close(g, gr, Sr, Sdr)

@@ -1,6 +1,6 @@
 """The alternative partitions of Sec. 4.3 and Sec. 4.5 (multi-resolution HEALPix superpixels per
 Galactic region; post-clustering binning of fitted parameter maps) fitted by the same kernels, on
-the 60% sky at nside 16, against oracle fits (acceptance as in test_gpu_fullsize)."""
+the 60% sky at nside 16, against oracle fits (acceptance as in tests/_fitcheck.py)."""
 import numpy as np
 import pytest
 
@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from synth import healpix, kmeans, partitions as pt, sky as S, workloads  # noqa: E402
-from tests._fitcheck import sampled_fit_check  # noqa: E402
+from tests._fitcheck import sampled_fit_check, stored_refs  # noqa: E402
 from tests._inputs import Case, pack  # noqa: E402
 
 NSIDE = 16
@@ -40,13 +40,13 @@ def _fit(csx, wl):
 
 
 def test_multires_configuration(csx):
-    pix, sk = _regions_sky()
-    lab, K = pt.multires_labels(NSIDE, pix, levels=((4, 4, 8), (0, 2, 4), (1, 1, 2)))
-    wl = workloads.Workload("multires16", sk, K[None], lab[None], 2, "separable")
+    from tests.golden import make_fit_refs as mk
+    wl = mk._multires16()
     case, res = _fit(csx, wl)
-    worst, fl, vfl, unc, jt = sampled_fit_check(csx, case, res, [0, 1])
-    print("K", K.tolist(), "worst |err|/tol %.3f; floors %d/%d; unconstrained %d; joint %d"
-          % (worst, fl, vfl, unc, jt))
+    # stored oracle fits (tests/golden/make_fit_refs.py): P = 517, minutes per oracle fit
+    picks, refs = stored_refs("multires16", case)
+    worst, alt = sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=refs)
+    print("K", wl.K[0].tolist(), "worst |err|/tol %.3f; alternative optima %d" % (worst, alt))
 
 
 def test_post_clustering_binning(csx):
@@ -56,8 +56,12 @@ def test_post_clustering_binning(csx):
     lab0 = np.stack([kmeans.patch_labels(vec, int(k), key="regions%d" % NSIDE) for k in Kk])
     wl0 = workloads.Workload("kmeans16", sk, Kk[None].astype(np.int32), lab0[None].astype(np.int32),
                              1, "separable")
-    _, res0 = _fit(csx, wl0)
-    beta = res0["beta"].cpu().numpy().astype(np.float64)
+    # the binned labels are oracle inputs too, so they come from the oracle's fit of the K-means
+    # configuration (not from the CUDA path's)
+    from oracle import fit as ofit
+    c0 = Case(wl0, "separable")
+    beta, _, _ = ofit.fit(c0.nu, c0.d64(0), c0.ninv64, lab0, Kk, wl0.beta0(0), workloads.LOWER,
+                          workloads.UPPER)
     offs = np.concatenate([[0], np.cumsum(Kk)])
     labs, Ks = [], []
     for j in range(3):
@@ -69,6 +73,5 @@ def test_post_clustering_binning(csx):
     wl = workloads.Workload("binned16", sk, Kb[None], np.stack(labs)[None].astype(np.int32), 2,
                             "separable")
     case, res = _fit(csx, wl)
-    worst, fl, vfl, unc, jt = sampled_fit_check(csx, case, res, [0, 1])
-    print("K", Kb.tolist(), "worst |err|/tol %.3f; floors %d/%d; unconstrained %d; joint %d"
-          % (worst, fl, vfl, unc, jt))
+    worst, alt = sampled_fit_check(csx, case, res, [0, 1], max_alternative=0)
+    print("K", Kb.tolist(), "worst |err|/tol %.3f; alternative optima %d" % (worst, alt))

@@ -1,7 +1,8 @@
 """Host-side logic of the multi-process path, on CPU with the gloo backend (world size 2):
 the contiguous chunking of problems (Sec. 3.1) and the one exchange of the path, the all-gather of
-per-configuration V_tot for the global selection; checked against the oracle's selection over the
-concatenated values. No GPU is used."""
+every rank's per-problem metric rows for the global selection (which csx_select then makes on the
+device); the gathered rows are checked against the full list and the oracle's selection over them.
+No GPU is used."""
 import os
 import socket
 
@@ -19,6 +20,17 @@ def _free_port():
     return port
 
 
+def _rows(nconf, nreal):
+    """Metric rows of nconf configurations x nreal problems: SYS_SQ and STAT slots set, a tie
+    between configurations 2 and 7 at the smallest total."""
+    rng = np.random.default_rng(5)
+    m = np.zeros((nconf * nreal, 8))
+    m[:, 0] = rng.random(nconf * nreal)
+    m[:, 1] = rng.random(nconf * nreal)
+    m[7 * nreal:8 * nreal] = m[2 * nreal:3 * nreal] = 0.0
+    return m
+
+
 def _worker(rank, world, port, q):
     import torch.distributed as dist
     from paper_2604_08463_b300 import csx
@@ -26,13 +38,11 @@ def _worker(rank, world, port, q):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        n = 11
-        lo, hi = csx.chunk(n, world, rank)
-        rng = np.random.default_rng(5)
-        v = rng.random(n)
-        v[7] = v[2] = v.min() - 0.5  # a tie: the lower index must win
-        allv, best = csx.gather_select(torch.tensor(v[lo:hi]))
-        q.put((rank, lo, hi, allv.numpy().tolist(), best))
+        nconf, nreal = 11, 3
+        lo, hi = csx.chunk(nconf, world, rank)  # whole configurations per rank
+        m = _rows(nconf, nreal)
+        allm = csx.gather_metrics(torch.tensor(m[lo * nreal:hi * nreal]))
+        q.put((rank, lo, hi, allm.numpy().tolist()))
     finally:
         dist.destroy_process_group()
 
@@ -49,7 +59,7 @@ def test_chunk_covers_every_problem_once():
         csx.chunk(5, 2, 2)
 
 
-def test_gather_select_gloo_two_ranks():
+def test_gather_metrics_gloo_two_ranks():
     import multiprocessing as mp
     from oracle import reconstruct as rc
     ctx = mp.get_context("spawn")
@@ -62,15 +72,14 @@ def test_gather_select_gloo_two_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    rng = np.random.default_rng(5)
-    v = rng.random(11)
-    v[7] = v[2] = v.min() - 0.5
-    # the oracle's selection on the same values: argmin, ties to the lowest index
-    metrics = [[{"sys_sq": 2.0 * x, "stat": 0.0}] for x in v]
-    vref, bref = rc.total_residual_variance(metrics, 1)
-    assert bref == 2
-    spans = sorted((lo, hi) for _, lo, hi, _, _ in out)
+    nconf, nreal, npix = 11, 3, 1
+    full = _rows(nconf, nreal)
+    spans = sorted((lo, hi) for _, lo, hi, _ in out)
     assert spans == [(0, 5), (5, 11)]
-    for _, _, _, allv, best in out:
-        np.testing.assert_array_equal(np.array(allv), vref)
-        assert best == bref
+    for _, _, _, allm in out:
+        np.testing.assert_array_equal(np.array(allm), full)  # every row, in rank order
+    # the oracle's selection over the gathered rows: argmin, ties to the lowest index
+    metrics = [[{"sys_sq": full[c * nreal + n, 0], "stat": full[c * nreal + n, 1]}
+                for n in range(nreal)] for c in range(nconf)]
+    vref, bref = rc.total_residual_variance(metrics, npix)
+    assert bref == 2 and vref[7] == vref[2]

@@ -85,3 +85,36 @@ def test_noalloc_second_configuration_and_size_limit(csx):
         ctypes.c_void_p(Lb.data_ptr()), ctypes.c_void_p(gb.data_ptr()), None)
     assert rc == -1
     assert b"static buffer" in csx.lib().csx_last_error()
+
+
+def test_noalloc_python_wrapper_and_host_refusals(csx):
+    # the Python wrapper passes caller-owned outputs straight through: same results as the
+    # allocating call
+    K = (7, 3, 5)
+    case = small_case(nside=8, K=K, nreal=2, noise="separable")
+    model, sky, labels = case.gpu()
+    lab = labels[0].contiguous()
+    beta = torch.tensor(workloads.random_points(np.array(K), 2, seed=11), dtype=torch.float32,
+                        device="cuda")
+    L = torch.empty(2, dtype=torch.float64, device="cuda")
+    g = torch.empty((2, sum(K)), dtype=torch.float32, device="cuda")
+    out = csx.spectral_grad_noalloc(model, sky, lab, K, beta, L, g)
+    assert out[0] is L and out[1] is g
+    Lr, gr = csx.spectral_grad(model, sky, lab, K, beta)
+    torch.cuda.synchronize()
+    _close(L, g, Lr, gr)
+    # outputs of the wrong type or shape, or an input that would need converting, are refused
+    # before anything reaches the device
+    with pytest.raises(ValueError, match="L must be"):
+        csx.spectral_grad_noalloc(model, sky, lab, K, beta, L.to(torch.float32), g)
+    with pytest.raises(ValueError, match="grad must be"):
+        csx.spectral_grad_noalloc(model, sky, lab, K, beta, L, g[:, :-1].contiguous())
+    with pytest.raises(ValueError, match="beta must be"):
+        csx.spectral_grad_noalloc(model, sky, lab, K, beta.double(), L, g)
+    # a patch count above CSX_MAX_K is refused by the C entry point
+    Kbad = np.array([1 << 25, 2, 2], dtype=np.int32)
+    rc = csx.lib().csx_spectral_grad_noalloc(
+        ctypes.byref(model.c), ctypes.byref(sky.c), ctypes.c_void_p(lab.data_ptr()),
+        Kbad.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 1, ctypes.c_void_p(beta.data_ptr()),
+        ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(g.data_ptr()), None)
+    assert rc == -1 and b"K_j" in csx.lib().csx_last_error()
