@@ -33,14 +33,22 @@ os.environ.setdefault("CSX_KMEANS_CACHE", os.path.join(ROOT, ".cache", "kmeans")
 METRIC = "config fits/s & cluster-pixel L+grad L evals/s at nside64 vs plain form; % HBM peak"
 SCAN = dict(nside=64, nconf=1000, kmax=500, nreal=10, b_cut_deg=20.0)
 BYTES_PER_PIXEL_EVAL = 120 + 12 + 4   # 15 bands x Q,U float32 + 3 int32 labels + hit weight
-BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12  # residual moments (R, C, Q) + cell labels
+# algorithmic bytes of one cell evaluation of the moment path: a cell's 120 unique second-moment
+# entries (15 x 15 symmetric, float32) and its three int32 patch labels. The implementation keeps
+# residual moments about a reference point instead (R 120 + C 45 + Q 6 floats: 696 B with labels),
+# for precision; the roofline counts the algorithmic figure.
+BYTES_PER_CELL_EVAL = 480 + 12
+IMPL_BYTES_PER_CELL_EVAL = 4 * (120 + 45 + 6) + 12
 FLOPS_PER_CELL_EVAL = 4600   # FP32 operations of one cell's chi2 + gradient (FMA = 2)
 FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (FMA = 2)
-# DRAM bytes (read + write) per unit from the committed ncu captures (profiles/): the persistent
-# fit per cell evaluation (1000-problem scan, 47.2 M cell evaluations, scaled by units), the
+# DRAM bytes (read + write) per unit from ncu captures of the current kernels (None until the
+# kernel has been captured since its last change): the persistent fit per cell evaluation, the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
-TRAFFIC_FIT_PER_CELL_EVAL = 979.5
+TRAFFIC_FIT_PER_CELL_EVAL = None
 TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.5, "L": 129.5}
+TRAFFIC_CAPTURE = {"fit": None,
+                   "stream": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_spectral_tma, "
+                             "full-sky nside 64, 100 realizations, per pixel evaluation"}
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -276,8 +284,8 @@ def run_csx(args):
         res = csx.fit_batch(model, sky, labels, K, beta0, **opts)
         rec = csx.reconstruct(model, sky, labels, K, res["beta"], d_fg=fg, metrics=True)
         vt, best = csx.select(rec["metrics"], nconf, nreal)
-        if dist:  # the path's one exchange: V_tot of every rank's configurations, global argmin
-            csx.gather_select(vt)
+        if dist:  # the path's one exchange: every rank's metric rows, then the global selection
+            csx.gather_select(rec["metrics"], nreal)
         return res, rec, vt, best
 
     # the clock sampler starts before the warm-up: starting nvidia-smi stalls CUDA launches briefly
@@ -316,7 +324,7 @@ def run_csx(args):
         t = time.perf_counter()
         vt, best = csx.select(rec["metrics"], nconf, nreal)
         if dist:
-            csx.gather_select(vt)
+            csx.gather_select(rec["metrics"], nreal)
         host_s["select"] += time.perf_counter() - t
         rec_ev[k][1].record(stream)
         evals.append(res["nevals"])
@@ -398,6 +406,8 @@ def run_csx(args):
                                  "frac_lower": float((dL < 0).mean())}}
 
     streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
+    fullsky = fullsky_fit_rates(csx) if (rank == 0 and not args.no_fullsky) else None
+    pipeline = pipeline_rates(csx) if (rank == 0 and not args.no_pipeline) else None
     kmeans_gpu = kmeans_rates(csx, inp) if (rank == 0 and not args.no_kmeans) else None
     spectra = (spectra_rates(csx, inp, model, sky, labels, fg, res["beta"])
                if (rank == 0 and not args.no_spectra) else None)
@@ -460,7 +470,8 @@ def run_csx(args):
     # DRAM traffic of one fit launch from the ncu capture (moment path only), scaled by units
     # the DRAM traffic per cell evaluation was captured with 128-thread CTAs
     traffic = (TRAFFIC_FIT_PER_CELL_EVAL * unit_evals
-               if path == "moment" and opts["threads"] in (0, 128) else None)
+               if TRAFFIC_FIT_PER_CELL_EVAL and path == "moment" and opts["threads"] in (0, 128)
+               else None)
     frac_mem, frac_alu = achieved / hbm, achieved_tf / fp32_peak
     if frac_alu >= frac_mem:
         roof = {"kernel": "k_fit (persistent fit)", "bound": "alu", "achieved": achieved_tf,
@@ -479,10 +490,8 @@ def run_csx(args):
                 "alu_side": {"achieved_tflops": achieved_tf, "peak_tflops": fp32_peak,
                              "frac": frac_alu}}
     roof["unit_kind"] = "cell evaluations" if path == "moment" else "pixel evaluations"
-    roof["traffic_source"] = ("profiles/k_fit_moment_scan_nside64.md (ncu, 1000-problem case, "
-                              "scaled by cell evaluations)" if traffic else None)
-    roof["limiter"] = ("latency: per-thread cell evaluations wait on moment loads "
-                       "(ncu long-scoreboard stalls; DRAM 8%, issue 35% active)")
+    roof["traffic_source"] = TRAFFIC_CAPTURE["fit"] if traffic else None
+    roof["impl_bytes_per_unit"] = IMPL_BYTES_PER_CELL_EVAL if path == "moment" else None
     line = {
         "metric": METRIC,
         "value": world * nprob / (ms_max * 1e-3),
@@ -515,6 +524,8 @@ def run_csx(args):
         "adatopk_fit": ada,
         "kmeans": kmeans_gpu,
         "residual_spectra": spectra,
+        "fullsky_fit": fullsky,
+        "pipeline": pipeline,
         "roofline": roof,
         "cpu_baseline": cpu_base,
         "e2e": e2e,
@@ -557,7 +568,10 @@ def streaming_rates(csx, hbm, ncall=20):
            "pixels_per_call": units, "bytes_per_pixel": BYTES_PER_PIXEL_EVAL,
            "timing": "CUDA events around %d calls (tables kernel + memsets + streaming kernel)"
                      % ncall}
+    from paper_2604_08463_b300 import autotune
     for name, fn in (("L_and_grad", csx.spectral_grad), ("L", csx.spectral_like)):
+        # tile schedule chosen by timing every built schedule on this call shape (left in force)
+        sched, entry = autotune.tune_stream(csx, model, sky, lab, K, beta, grad=name == "L_and_grad")
         for _ in range(3):
             fn(model, sky, lab, K, beta)
         torch.cuda.synchronize()
@@ -571,10 +585,13 @@ def streaming_rates(csx, hbm, ncall=20):
         ms = e0.elapsed_time(e1) / ncall
         gbs = units * BYTES_PER_PIXEL_EVAL / (ms * 1e-3) / 1e9
         out[name] = {"ms_per_call": ms, "cluster_pixel_evals_per_s": units / (ms * 1e-3),
+                     "schedule": {"chosen": "%d/%d" % sched, "candidates_ms": entry["ms"],
+                                  "unit": "pixels per tile / pipeline stages"},
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                   "frac": gbs / hbm,
                                   "traffic": TRAFFIC_STREAM_PER_PIXEL[name] * units,
-                                  "traffic_source": "profiles/k_spectral_tma_fullsky_nside64.md"}}
+                                  "traffic_source": TRAFFIC_CAPTURE["stream"]}}
+    csx.stream_schedule(0, 0)
     del d, sky
     torch.cuda.empty_cache()
     return out
@@ -624,6 +641,146 @@ def kmeans_rates(csx, inp):
                                "labelings_per_s": len(big) / host_s, "processes": 1},
             "iters_mean": float(iters.float().mean()), "mismatched_vs_generator": mismatched,
             "timing": "CUDA events around one csx_kmeans launch (one CTA per labeling)"}
+
+
+PIPE = dict(nside=64, nconf=4000, kmax=1000, nreal=10, b_cut_deg=20.0, seed=4, chunk=250, lmax=150)
+
+
+def pipeline_rates(csx):
+    """The full pipeline at nside 64 with the |b| > 20 deg cut: 4000 patch configurations with
+    (K_bd, K_Td, K_bs) log-uniform in 1..1000, 10 noise realizations each (the workload's 50
+    realizations scaled to 10 to keep the bench within minutes; the cost per problem does not
+    depend on R). Steps, each timed with CUDA events: GPU spherical K-means of every distinct K
+    (bit-exact with the seeded host generator, whose ~900 labelings would take hours on the host;
+    starting pixels drawn on the host), the batched adjoint fit of all 40000 problems, the
+    reconstruction with the systematic and statistical residual metrics, the selection of the best
+    configuration, and the residual spectra (l <= 150) of every configuration in chunks of 250."""
+    import numpy as np
+    import torch
+    from synth import healpix, kmeans as km, sky as S, workloads
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    pix = healpix.galactic_cut(PIPE["nside"], PIPE["b_cut_deg"])
+    sk = S.make_sky(PIPE["nside"], pix=pix, truth="smooth", hitcount=True)
+    vec = healpix.unit_vectors(PIPE["nside"])[pix]
+    n, nconf, nreal = vec.shape[0], PIPE["nconf"], PIPE["nreal"]
+    kreq_all = workloads.sample_patch_counts(nconf, PIPE["kmax"], seed=PIPE["seed"])
+    vd = torch.from_numpy(vec).to(dev)
+    d = torch.from_numpy(sk.data_stack(nreal)).to(dev)
+    nb = np.zeros(16, np.float32)
+    nb[:sk.nfreq] = sk.ninv_band
+    sky = csx.Sky(d, noise="separable", ninv_band=nb, w=torch.from_numpy(sk.w.astype(np.float32)).to(dev))
+    model = csx.Model(sk.nu)
+    fg = torch.from_numpy(sk.padded(sk.foreground)).to(dev)
+    s_true = torch.tensor(np.asarray(sk.cmb, dtype=np.float32), device=dev)
+    plan = csx.ShtPlan(PIPE["nside"], PIPE["lmax"], sk.pix)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def run(kreq):
+        times = {}
+        nc = kreq.shape[0]
+
+        def timed(name, fn):
+            a, b = ev(), ev()
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            times[name] = a.elapsed_time(b)
+            return out
+
+        ks = sorted({int(k) for k in kreq.ravel()})
+        init = [km.init_indices(n, k, 100 + k) for k in ks if 1 < k < n]
+        lab_k, _ = timed("kmeans_ms", lambda: csx.kmeans(vd, ks, init))
+        pos = {k: i for i, k in enumerate(ks)}
+        # per-configuration label array [C, 3, npix] from the labelings of the distinct K (input
+        # assembly), and each labeling's patch count
+        idx = torch.tensor([[pos[int(k)] for k in row] for row in kreq], device=dev)
+        labels = lab_k[idx].contiguous()
+        Keff = (lab_k.amax(dim=1) + 1).cpu().numpy()[idx.cpu().numpy()].astype(np.int32)
+        P = Keff.sum(axis=1)
+        beta0 = torch.tensor(np.concatenate([np.tile(np.concatenate(
+            [np.full(int(Keff[c, j]), workloads.BETA0[j]) for j in range(3)]), nreal)
+            for c in range(nc)]).astype(np.float32), device=dev)
+        res = timed("fit_ms", lambda: csx.fit_batch(model, sky, labels, Keff, beta0))
+        rec = timed("reconstruct_ms", lambda: csx.reconstruct(model, sky, labels, Keff, res["beta"],
+                                                              d_fg=fg, metrics=True))
+        vt, best = timed("select_ms", lambda: csx.select(rec["metrics"], nc, nreal))
+        offs, _ = csx.param_offsets(Keff, nreal)
+        offs = np.append(offs, int(P.sum()) * nreal)
+
+        def spectra():
+            out = []
+            for c0 in range(0, nc, PIPE["chunk"]):
+                c1 = min(nc, c0 + PIPE["chunk"])
+                b = res["beta"][int(offs[c0 * nreal]):int(offs[c1 * nreal])]
+                r = csx.reconstruct(model, sky, labels[c0:c1], Keff[c0:c1], b, d_fg=fg, s_hat=True,
+                                    r_sys=True, metrics=False)
+                out.append(csx.residual_spectra(plan, r["s_hat"], s_true, r["r_sys"], nreal)["stat"])
+                del r
+            return out
+        timed("spectra_ms", spectra)
+        return times, res, best, Keff, P, len(ks)
+
+    run(kreq_all[:100])  # warm-up: scratch buffers grown, kernels loaded
+    times, res, best, Keff, P, nks = run(kreq_all)
+    ks = range(nks)
+    total = sum(times.values())
+    st = res["status"].cpu().numpy()
+    return {"workload": "pipeline_nside64_b20_C%d_K%d_R%d" % (nconf, PIPE["kmax"], nreal),
+            "configurations": nconf, "realizations": nreal, "problems": nconf * nreal,
+            "mean_P": float(P.mean()), "max_P": int(P.max()), "distinct_K": len(ks),
+            "stage_ms": times, "total_ms": total,
+            "configurations_per_s": nconf / (total * 1e-3),
+            "latency_per_configuration_ms": total / nconf,
+            "fits_per_s": nconf * nreal / (times["fit_ms"] * 1e-3),
+            "fit_stats": {"converged": int((st == 0).sum()), "max_iter": int((st == 1).sum()),
+                          "line_search": int((st == 3).sum()),
+                          "iters_mean": float(res["iters"].float().mean().item())},
+            "best_configuration": int(best.item()), "K_best": Keff[int(best.item())].tolist(),
+            "timing": "CUDA events around each stage, one pass after a warm-up pass on 100 "
+                      "configurations; labels assembled from the distinct labelings on the device"}
+
+
+FULLSKY = dict(nside=64, K=(100, 20, 30), nreal=100)
+
+
+def fullsky_fit_rates(csx):
+    """The full-sky nside-64 configuration with K = (100, 20, 30) and 100 noise realizations (hit-count
+    noise, smooth truth): the batched adjoint fit of the 100 problems followed by the W d
+    reconstruction of every realization (s_hat for all pixels, Q and U, three components), each
+    timed with CUDA events."""
+    import numpy as np
+    import torch
+    from synth import workloads
+    wl = workloads.fullsky(FULLSKY["nside"], FULLSKY["K"], nreal=FULLSKY["nreal"])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    d = torch.from_numpy(wl.data()).to(dev)
+    nb = np.zeros(16, np.float32)
+    nb[:wl.sky.nfreq] = wl.sky.ninv_band
+    sky = csx.Sky(d, noise="separable", ninv_band=nb,
+                  w=torch.from_numpy(wl.sky.w.astype(np.float32)).to(dev))
+    model = csx.Model(wl.sky.nu)
+    labels = torch.from_numpy(np.ascontiguousarray(wl.labels)).to(dev)
+    beta0 = torch.tensor(np.tile(wl.beta0(0), wl.nreal).astype(np.float32), device=dev)
+    out = {}
+    for k in range(2):  # warm-up, then timed
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        res = csx.fit_batch(model, sky, labels, wl.K, beta0)
+        e[1].record(stream)
+        rec = csx.reconstruct(model, sky, labels, wl.K, res["beta"], s_hat=True, metrics=False)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        out = {"fit_ms": e[0].elapsed_time(e[1]), "reconstruct_ms": e[1].elapsed_time(e[2])}
+    st = res["status"].cpu().numpy()
+    del rec, d, sky
+    torch.cuda.empty_cache()
+    return dict(out, workload="fullsky_nside64_K%s_R%d" % (list(FULLSKY["K"]), wl.nreal),
+                fits_per_s=wl.nreal / (out["fit_ms"] * 1e-3),
+                converged=int((st == 0).sum()),
+                iters_mean=float(res["iters"].float().mean().item()))
 
 
 SPECTRA = {"nconf": 100, "lmax": 150}
@@ -770,6 +927,8 @@ def main():
     ap.add_argument("--no-adatopk", action="store_true", help="skip the AdaTopK comparison fit")
     ap.add_argument("--no-kmeans", action="store_true", help="skip the GPU K-means rates")
     ap.add_argument("--no-spectra", action="store_true", help="skip the residual-spectra rates")
+    ap.add_argument("--no-fullsky", action="store_true", help="skip the full-sky fit leg")
+    ap.add_argument("--no-pipeline", action="store_true", help="skip the full-pipeline leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -146,6 +146,17 @@ int csx_release(void);
  */
 int csx_device_status(void* stream);
 
+/*
+ * Tile schedule of the streaming likelihood kernel (csx_spectral_like, csx_spectral_grad and
+ * csx_spectral_grad_noalloc): pixels per tile (= threads per CTA) and tensor-copy pipeline stages,
+ * for the launches that follow, in every thread and on every device. Built schedules:
+ * (128, 2) (the default), (64, 2), (64, 3), (128, 3), (128, 4), (256, 2); (0, 0) restores the
+ * default; (-1, -1) changes nothing. current: host int32[2] receiving the schedule in force, or
+ * NULL. The results do not depend on the schedule beyond FP32 rounding. Errors: CSX_EINVAL for a
+ * pair that is not built. A host-only call.
+ */
+int csx_stream_schedule(int32_t tile, int32_t stages, int32_t* current);
+
 /* Fill `o` with the defaults listed in csx_fit_opts. */
 int csx_fit_defaults(csx_fit_opts* o);
 

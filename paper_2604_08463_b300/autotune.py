@@ -136,3 +136,57 @@ def tune_fit(csx, model, sky, labels, K, beta0, solver: str = "lbfgs", grad_mode
         return e0.elapsed_time(e1)
 
     return choose(key, cands, timer, cache)
+
+
+# ------------------------------------------------------------------ streaming kernel schedule ----
+def stream_key(noise: str, npix: int, nprob: int, P: int, grad: bool) -> str:
+    """Cache key of a streaming call: noise model, gradient or not, and the powers of two nearest to
+    the pixel count, the number of problems and the parameter count."""
+    return "stream|%s|%s|n2^%d|q2^%d|P2^%d" % (noise, "grad" if grad else "like", _p2(npix),
+                                              _p2(nprob), _p2(P))
+
+
+def choose_schedule(key: str, cands, timer, cache=None, margin: float = MARGIN):
+    """The fastest (tile, stages) schedule for `key`: from the cache, else by timer(tile, stages) ->
+    ms for every candidate; the first candidate (the library default) is kept unless another is
+    faster by more than `margin`. Returns ((tile, stages), table entry)."""
+    table = _load(cache)
+    if key in table:
+        e = table[key]
+        return (e["tile"], e["stages"]), e
+    ms = {"%d/%d" % c: float(timer(*c)) for c in cands}
+    best = min(cands, key=lambda c: ms["%d/%d" % c])
+    if ms["%d/%d" % best] > (1.0 - margin) * ms["%d/%d" % cands[0]]:
+        best = cands[0]
+    e = {"tile": best[0], "stages": best[1], "ms": ms}
+    table[key] = e
+    _store(cache, table)
+    return (e["tile"], e["stages"]), e
+
+
+def tune_stream(csx, model, sky, labels, K, beta, grad: bool = True, ncall: int = 5, cache=None):
+    """Select the streaming kernel's tile schedule for calls shaped like this one (csx.spectral_grad
+    or csx.spectral_like of beta [nprob, P] on sky): each built schedule is timed with CUDA events
+    over `ncall` calls after one untimed call; the chosen schedule is left in force
+    (csx.stream_schedule). Returns ((tile, stages), table entry)."""
+    import torch
+    fn = csx.spectral_grad if grad else csx.spectral_like
+    key = stream_key(sky.noise, sky.npix, beta.shape[0], beta.shape[1], grad)
+
+    def timer(tile, stages):
+        csx.stream_schedule(tile, stages)
+        fn(model, sky, labels, K, beta)
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ncall):
+            fn(model, sky, labels, K, beta)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / ncall
+
+    sched, e = choose_schedule(key, list(csx.STREAM_SCHEDULES), timer, cache)
+    csx.stream_schedule(*sched)
+    return sched, e

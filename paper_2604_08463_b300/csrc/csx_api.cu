@@ -253,6 +253,15 @@ int csx_device_status(void* stream) {
   return CSX_OK;
 }
 
+int csx_stream_schedule(int32_t tile, int32_t stages, int32_t* current) {
+  if (tile != -1 || stages != -1) {
+    const int rc = set_stream_schedule(tile, stages);
+    if (rc) return rc;
+  }
+  if (current) get_stream_schedule(&current[0], &current[1]);
+  return CSX_OK;
+}
+
 int csx_fit_defaults(csx_fit_opts* o) {
   if (!o) return fail(CSX_EINVAL, "opts is NULL");
   std::memset(o, 0, sizeof(*o));

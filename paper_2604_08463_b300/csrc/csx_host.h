@@ -93,6 +93,9 @@ struct Spec64Args {
 int launch_spectral64(const Spec64Args& a, bool grad, cudaStream_t s);
 int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA, cudaStream_t s);
 int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s);
+// Tile schedule of the streaming kernel for the launches that follow (process-wide).
+int set_stream_schedule(int tile, int stages);
+void get_stream_schedule(int* tile, int* stages);
 // Synchronises `s`, returns (and clears) the count of bounded device waits that gave up.
 int device_timeouts(cudaStream_t s, unsigned* count);
 

@@ -28,20 +28,11 @@
 namespace csx {
 
 // Build-time tuning switches (the defaults are the measured best on B300):
-//   CSX_FIT_STAGE_MOMENTS  1: a cell's 171 moments are staged into shared memory by cp.async
-//                          before use; 0: read from global memory (L2) where used.
 //   CSX_FIT_MIN_BLOCKS     minimum resident 128-thread moment-path CTAs per SM asked of ptxas.
-//   CSX_FIT_PREFETCH       1: prefetch each thread's next cell's moments into L2.
 //   CSX_FIT_NEAR           step size (in xtol) below which the reference point first moves to
 //                          the current point (0: only at convergence).
-#ifndef CSX_FIT_STAGE_MOMENTS
-#define CSX_FIT_STAGE_MOMENTS 0
-#endif
 #ifndef CSX_FIT_NEAR
 #define CSX_FIT_NEAR 0.f
-#endif
-#ifndef CSX_FIT_PREFETCH
-#define CSX_FIT_PREFETCH 0
 #endif
 #ifndef CSX_FIT_MIN_BLOCKS
 #define CSX_FIT_MIN_BLOCKS 4
@@ -63,13 +54,48 @@ struct Ctx {
   float* smem;        // moment path: dynamic shared memory (build staging, then per-thread rows)
 };
 
+constexpr int LB_NV = 2 + 3 * MAXM;  // dot products fused into one reduction at a step's acceptance
+
 struct Shared {
   double red[16];
   double rho[MAXM], alpha[MAXM];
   float gacc[SMEM_P], hacc[SMEM_P];
   float stage[8][32];  // per-warp staging of warp_run_accum3
-  int cmd;             // the L-BFGS leader warp's request to the CTA (FitCmd)
+  // compact L-BFGS: s_i^T y_j and y_i^T y_j of the stored pairs (by slot), the direction's
+  // coefficients, and the per-warp partial sums of the fused dot products
+  double SY[MAXM][MAXM], YY[MAXM][MAXM];
+  float coefS[MAXM], coefY[MAXM];
+  double wpart[8][LB_NV];
+  double dots[LB_NV];
 };
+
+// Sums over the block of the per-thread FP32 partials part[v] whose bit v is set in `used`,
+// deterministic: a fixed shuffle tree in each warp, then the warps' sums in warp order in FP64
+// (thread v adds value v); one barrier pair for all of them. Totals in sh.dots[v].
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum_many(float (&part)[NV], unsigned long long used,
+                                               Shared& sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if ((used >> v) & 1ull) {
+      float x = part[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) sh.wpart[warp][v] = (double)x;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < NV; v += NT) {
+    if ((used >> v) & 1ull) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < NT / 32; ++w) t += sh.wpart[w][v];
+      sh.dots[v] = t;
+    }
+  }
+  __syncthreads();
+}
 
 // Gradient (and Gauss-Newton diagonal) accumulation without float atomics: each warp adds its
 // run totals to its own partial P-vector in program order (warp_run_accum3), and the vectors are
@@ -156,17 +182,17 @@ __device__ __forceinline__ float resid_exact(float d, float s0, float s1, float 
   return __fadd_rn(x, __fsub_rn(err, __fadd_rn(e1, e2)));
 }
 
-// Floats of the per-thread evaluation rows at the start of the dynamic shared memory (moment path:
-// N A_1 and N A_2 per thread, plus the staged moments with CSX_FIT_STAGE_MOMENTS); the warp
-// partials of the gradient follow them.
-template <int NT, int PATH>
-constexpr int fit_rows_floats() {
-  return PATH == CSX_PATH_MOMENT ? (30 + (CSX_FIT_STAGE_MOMENTS ? NM : 0)) * NT : 0;
-}
 
 __device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
 
-template <int NT, bool SEP>
+// Floats of the per-thread evaluation rows at the start of the dynamic shared memory (moment path:
+// N A_1 and N A_2 per thread); the warp partials of the gradient follow them.
+template <int NT, int PATH>
+constexpr int fit_rows_floats() {
+  return PATH == CSX_PATH_MOMENT ? 30 * NT : 0;
+}
+
+template <int NT, bool SEP, bool EXACT>
 __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* sv = smem + warp * BUILD_SMEM_PER_WARP;  // 32 pixel rows
@@ -248,9 +274,15 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
         const float su0 = tu0 - g.mu1 * su1 - g.mu2 * tu2;
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
-          const float a1 = sb[32 + f], a2 = sb[48 + f];
-          row[f] = (f < 15) ? resid_exact(dq[f], sq0, sq1, tq2, a1, a2) : 0.f;
-          row[20 + f] = (f < 15) ? resid_exact(du[f], su0, su1, tu2, a1, a2) : 0.f;
+          if (EXACT) {
+            const float a1 = sb[32 + f], a2 = sb[48 + f];
+            row[f] = (f < 15) ? resid_exact(dq[f], sq0, sq1, tq2, a1, a2) : 0.f;
+            row[20 + f] = (f < 15) ? resid_exact(du[f], su0, su1, tu2, a1, a2) : 0.f;
+          } else {  // in the Gram-Schmidt basis, rounded at the data's scale
+            const float c1 = sb[f], c2 = sb[16 + f];
+            row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2, fmaf(tq1, c1, tq0)) : 0.f;
+            row[20 + f] = (f < 15) ? du[f] - fmaf(tu2, c2, fmaf(tu1, c1, tu0)) : 0.f;
+          }
         }
         row[15] = sq0;
         row[16] = sq1;
@@ -336,12 +368,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
   for (int f = 0; f < 15; ++f) nsum += nb[f];
   float* row = c.smem + threadIdx.x;            // row[k * NT]: N A_1 (k = 0..14), N A_2 (15..29)
-#if CSX_FIT_STAGE_MOMENTS
-  float* ms = c.smem + 30 * NT + threadIdx.x;   // ms[e * NT]: the cell's 171 staged moments
-  constexpr int mst = NT;
-#else
   const int mst = c.ncell;
-#endif
   float acc = 0.f;  // per-thread sum over its few cells in FP32, FP64 across the block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* gwv = c.gw + (long long)warp * c.P;
@@ -363,36 +390,11 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const float* pdr = c.tabr + kd * NB;
     const float* btr = c.tabr + (c.Kd + kt) * NB;
     const float* ssr = c.tabr + (c.Kd + 2 * c.KT + ks) * NB;
-#if CSX_FIT_STAGE_MOMENTS
-    {
-      // stage the cell's moments into this thread's shared column: all 171 copies in flight at
-      // once, consumed after the table pass below (the cell's previous use of the column has
-      // completed: every read of it precedes this point in program order)
-      const float* Mc = c.mom + cell;
-      const long long st = c.ncell;
-#pragma unroll 19
-      for (int e = 0; e < NM; ++e) cp_async4(ms + e * NT, Mc + e * st);
-      cp_async_commit();
-    }
-#else
     const float* ms = c.mom + cell;
-#if CSX_FIT_PREFETCH
-    {
-      // bring the thread's next cell's moments towards L2 while this cell is evaluated (the
-      // moments of all resident problems exceed L2; a warp's prefetches cover whole lines)
-      const int nxt = cell + NT;
-      if (nxt < c.ncell) {
-        const float* mn = c.mom + nxt;
-#pragma unroll 9
-        for (int e = 0; e < NM; ++e)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(mn + (long long)e * c.ncell));
-      }
-    }
-#endif
-#endif
-    // M = A^T N A and Z = A_r^T N A
+    // M = A^T N A, Z = A_r^T N A and G = A^T N dA with dA = A - A_r (its first column is 0)
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
     float z10 = 0.f, z11 = 0.f, z12 = 0.f, z20 = 0.f, z21 = 0.f, z22 = 0.f;
+    float g01 = 0.f, g02 = 0.f, g11 = 0.f, g12 = 0.f, g21 = 0.f, g22 = 0.f;
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
@@ -412,10 +414,14 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       z20 = fmaf(r2, n, z20);
       z21 = fmaf(r2, t1, z21);
       z22 = fmaf(r2, t2, z22);
+      const float e1 = a1 - r1, e2 = a2 - r2;
+      g01 = fmaf(n, e1, g01);
+      g02 = fmaf(n, e2, g02);
+      g11 = fmaf(t1, e1, g11);
+      g12 = fmaf(t1, e2, g12);
+      g21 = fmaf(t2, e1, g21);
+      g22 = fmaf(t2, e2, g22);
     }
-#if CSX_FIT_STAGE_MOMENTS
-    cp_async_wait_all();
-#endif
     Chol3 ch;
     if (!chol3(nsum, m01, m02, m11, m12, m22, ch)) {
       acc += nan_f();
@@ -428,12 +434,17 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     v[2][0] = v[0][2];
     v[2][1] = v[1][2];
     const float Z[3][3] = {{nsum, m01, m02}, {z10, z11, z12}, {z20, z21, z22}};
-    // Y = M^-1 A^T N A_r = M^-1 Z^T ; D = A_r - A Y
-    float Y[3][3];
+    // D = P A_r = -P dA = A M^-1 A^T N dA - dA (P the N-orthogonal projector off the columns of A):
+    // its first column vanishes (the constant column lies in span A) and D is formed from dA, so it
+    // is exactly zero at the reference point and as accurate as dA near it (forming it as
+    // A_r - A M^-1 A^T N A_r would leave the FP32 inverse's error, eps cond M, on the signal-sized
+    // moments). Yd[k][j] = (M^-1 A^T N dA)[k][j + 1], j = 0, 1.
+    float Yd[3][2];
 #pragma unroll
-    for (int l = 0; l < 3; ++l)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) Y[l][k] = v[l][0] * Z[k][0] + v[l][1] * Z[k][1] + v[l][2] * Z[k][2];
+    for (int k = 0; k < 3; ++k) {
+      Yd[k][0] = v[k][0] * g01 + v[k][1] * g11 + v[k][2] * g21;
+      Yd[k][1] = v[k][0] * g02 + v[k][1] * g12 + v[k][2] * g22;
+    }
     // pass 1 over bands: G1 = D^T N D, t2 = tr(D^T N C), CtA = C^T N A
     float G1[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     float CtA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -441,24 +452,25 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
-      const float ar[3] = {1.f, pdr[f] * btr[f], ssr[f]};
+      const float e1 = a1 - pdr[f] * btr[f], e2 = a2 - ssr[f];
       const float na[3] = {nb[f], row[f * NT], row[(15 + f) * NT]};
       float D[3], C[3];
+      D[0] = 0.f;
+      D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
+      D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = ms[mom_index(f, 15 + k) * mst];
-      }
+      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * mst];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 1; k < 3; ++k) {
         const float nd = nb[f] * D[k];
         tdc = fmaf(nd, C[k], tdc);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) {
-          G1[k][l] = fmaf(nd, D[l], G1[k][l]);
-          CtA[k][l] = fmaf(C[k], na[l], CtA[k][l]);
-        }
+        for (int l = 1; l < 3; ++l) G1[k][l] = fmaf(nd, D[l], G1[k][l]);
       }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) CtA[k][l] = fmaf(C[k], na[l], CtA[k][l]);
     }
     // B = R N A row by row, A^T N R N A, tr(N R), and the gradient part carried by B: with
     // E = U + C Z + B - A Psi, the B term of E M^-1 in band i is sum_l B[i][l] M^-1[l][k]
@@ -518,13 +530,13 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = pd[f] * bt[f], a2 = ss[f];
-      const float ar[3] = {1.f, pdr[f] * btr[f], ssr[f]};
+      const float e1 = a1 - pdr[f] * btr[f], e2 = a2 - ssr[f];
       float D[3], C[3];
+      D[0] = 0.f;
+      D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
+      D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        D[k] = ar[k] - fmaf(a2, Y[2][k], fmaf(a1, Y[1][k], Y[0][k]));
-        C[k] = ms[mom_index(f, 15 + k) * mst];
-      }
+      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * mst];
       float E[3];
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
@@ -669,104 +681,63 @@ __device__ void fd_gradient(const FitArgs& a, Ctx& c, Shared& sh, const float* z
 }
 
 // ------------------------------------------------------------------------ the fit --------------
-// Moment path: make the current point c.x the reference point and rebuild the cell moments.
+// Moment path: make the current point c.x the reference point and rebuild the cell moments. The
+// first build of a fit (at the start point, far from the optimum) forms the residuals in the
+// Gram-Schmidt basis; every later one (a move of the reference point near convergence) forms them
+// exactly (resid_exact), which the precision of the last iterations' gradients rests on.
 template <int NT, int NOISE>
-__device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem) {
+__device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem, bool exact = true) {
   for (int i = threadIdx.x; i < c.P; i += NT) c.xr[i] = c.x[i];
   __syncthreads();
   fill_tables<NT>(a, c, c.xr, c.tabr);
-  return build_moments<NT, NOISE == CSX_NOISE_SEPARABLE>(a, c, smem, sh);
-}
-
-// Collective steps of the L-BFGS driver. The optimiser's vector algebra runs on one leader warp
-// (warp 0), with warp-shuffle reductions and no block barrier; the other warps only take part in
-// the steps that need the whole CTA -- likelihood evaluations, moment builds, finite-difference
-// gradients -- which the leader requests through shared memory (fit_cmd).
-enum FitCmd { CMD_DONE = 0, CMD_EVAL, CMD_EVAL_H, CMD_RECENTRE, CMD_FD_Z, CMD_FD_ZT };
-
-template <int NT, int PATH, int GMODE, int NOISE>
-__device__ double run_cmd(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int cmd, double& dnd) {
-  switch (cmd) {
-    case CMD_EVAL: return objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
-    case CMD_EVAL_H: return objective<NT, PATH, GMODE, NOISE, true>(a, c, sh, dnd);
-    case CMD_RECENTRE: return PATH == CSX_PATH_MOMENT ? recentre<NT, NOISE>(a, c, sh, smem) : 0.0;
-    case CMD_FD_Z:
-      if (GMODE == CSX_GRAD_FD) fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
-      return 0.0;
-    case CMD_FD_ZT:
-      if (GMODE == CSX_GRAD_FD) fd_gradient<NT, NOISE>(a, c, sh, c.zt, c.gt);
-      return 0.0;
-    default: return 0.0;
-  }
-}
-
-// Leader side: publish the command, meet the helpers at a barrier, run the step with them. The
-// leader's earlier writes (c.x) are visible to every thread after the barrier.
-template <int NT, int PATH, int GMODE, int NOISE>
-__device__ double fit_cmd(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int cmd, double& dnd) {
-  if (threadIdx.x == 0) sh.cmd = cmd;
-  __syncthreads();
-  return run_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, cmd, dnd);
-}
-
-template <int NT, int PATH, int GMODE, int NOISE>
-__device__ void fit_helper(const FitArgs& a, Ctx& c, Shared& sh, float* smem) {
-  double dnd = 0.0;
-  for (;;) {
-    __syncthreads();  // the leader's fit_cmd
-    const int cmd = sh.cmd;
-    if (cmd == CMD_DONE) break;
-    (void)run_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, cmd, dnd);
-  }
+  constexpr bool SEP = NOISE == CSX_NOISE_SEPARABLE;
+  return exact ? build_moments<NT, SEP, true>(a, c, smem, sh)
+               : build_moments<NT, SEP, false>(a, c, smem, sh);
 }
 
 template <int NT, int PATH, int GMODE, int NOISE>
 __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int q,
                             long long poff) {
-  if (threadIdx.x >= 32) {
-    fit_helper<NT, PATH, GMODE, NOISE>(a, c, sh, smem);
-    return;
-  }
   const int P = c.P;
-  const int ln = threadIdx.x;  // lane of the leader warp
+  const int tid = threadIdx.x;
   const int m = a.history;
-  auto cmd = [&](int k, double& dn) { return fit_cmd<NT, PATH, GMODE, NOISE>(a, c, sh, smem, k, dn); };
   // start point, clamped into the box
-  for (int i = ln; i < P; i += 32) {
+  for (int i = tid; i < P; i += NT) {
     const int t = ptype(c, i);
     c.x[i] = fminf(fmaxf(a.beta0[poff + i], a.lower[t]), a.upper[t]);
   }
+  __syncthreads();
   double dnd = 0.0;
   int recentres = 0;
-  if (PATH == CSX_PATH_MOMENT) dnd = cmd(CMD_RECENTRE, dnd);
-  double f = cmd(CMD_EVAL_H, dnd);
+  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem, false);
+  double f = objective<NT, PATH, GMODE, NOISE, true>(a, c, sh, dnd);
   int nev = 1;  // likelihood evaluations (each forward pass of a finite difference counts once)
   int status = CSX_FIT_MAXITER, it = 0;
   if (!isfinite(f)) {
-    for (int i = ln; i < P; i += 32) a.beta_out[poff + i] = c.x[i];
-    if (ln == 0) {
+    for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.x[i];
+    if (tid == 0) {
       a.L_out[q] = (double)nan_f();
       a.status[q] = CSX_FIT_NONPHYSICAL;
       a.iters[q] = 0;
       if (a.nevals) a.nevals[q] = nev;
     }
-    (void)cmd(CMD_DONE, dnd);
+    __syncthreads();
     return;
   }
   // scaling by sqrt of the Gauss-Newton diagonal
   float hm = 0.f;
-  for (int i = ln; i < P; i += 32) hm = fmaxf(hm, isfinite(c.hacc[i]) ? c.hacc[i] : 0.f);
-  hm = warp_max(hm);
+  for (int i = tid; i < P; i += NT) hm = fmaxf(hm, isfinite(c.hacc[i]) ? c.hacc[i] : 0.f);
+  hm = block_max<NT>(hm, reinterpret_cast<float*>(sh.red));
   const float hfloor = fmaxf(1e-12f * hm, 1e-30f);
-  for (int i = ln; i < P; i += 32) {
+  for (int i = tid; i < P; i += NT) {
     const float h = c.hacc[i];
     c.hs[i] = sqrtf((isfinite(h) && h > hfloor) ? h : hfloor);
     c.z[i] = c.hs[i] * c.x[i];
     if (GMODE == CSX_GRAD_ADJOINT) c.g[i] = c.gacc[i] / c.hs[i];
   }
-  __syncwarp();
+  __syncthreads();
   if (GMODE == CSX_GRAD_FD) {
-    (void)cmd(CMD_FD_Z, dnd);
+    fd_gradient<NT, NOISE>(a, c, sh, c.z, c.g);
     nev += 2 * P;
   }
 
@@ -775,45 +746,71 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
   float last_step = 1e30f;
   const double delta = 0.1, sigma = 0.9;
   for (it = 0; it < a.max_iter; ++it) {
-    // ---- direction: two-loop recursion on the free-set gradient --------------------------
-    for (int i = ln; i < P; i += 32) {
+    // ---- direction: L-BFGS inverse Hessian times the free-set gradient ----------------------
+    // compact form (Byrd, Nocedal and Schnabel 1994), the same product as the two-loop recursion:
+    //   H p = gamma p + S a - gamma Y t,  t = R^-1 S^T p,  a = R^-T ((D + gamma Y^T Y) t - gamma Y^T p)
+    // with S, Y the stored pairs oldest first, R the upper triangle of S^T Y and D its diagonal;
+    // the 2 count dot products S^T p, Y^T p are formed in one pass and one block reduction.
+    for (int i = tid; i < P; i += NT) {
       const int t = ptype(c, i);
       const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
       const float gi = c.g[i];
       const bool act = (c.z[i] <= zl && gi > 0.f) || (c.z[i] >= zu && gi < 0.f);
       c.p[i] = act ? 0.f : gi;
     }
-    __syncwarp();
-    for (int j = 0; j < count; ++j) {
-      const int k = (head - 1 - j + m) % m;
-      const float* Sk = c.S + (long long)k * a.Pmax;
-      float dotf = 0.f;  // per-lane partial in FP32, FP64 across the warp
-      for (int i = ln; i < P; i += 32) dotf = fmaf(Sk[i], c.p[i], dotf);
-      const double dot = warp_sum((double)dotf);
-      const double al = sh.rho[k] * dot;
-      if (ln == 0) sh.alpha[k] = al;
-      const float* Yk = c.Y + (long long)k * a.Pmax;
-      for (int i = ln; i < P; i += 32) c.p[i] -= (float)al * Yk[i];
-      __syncwarp();
-    }
-    for (int i = ln; i < P; i += 32) c.p[i] *= (float)gamma;
-    __syncwarp();
-    for (int j = count - 1; j >= 0; --j) {
-      const int k = (head - 1 - j + m) % m;
-      const float* Yk = c.Y + (long long)k * a.Pmax;
-      float dotf = 0.f;
-      for (int i = ln; i < P; i += 32) dotf = fmaf(Yk[i], c.p[i], dotf);
-      const double dot = warp_sum((double)dotf);
-      const double be = sh.rho[k] * dot;
-      const float* Sk = c.S + (long long)k * a.Pmax;
-      const float coef = (float)(sh.alpha[k] - be);
-      for (int i = ln; i < P; i += 32) c.p[i] += coef * Sk[i];
-      __syncwarp();
+    if (count > 0) {
+      const int old = head - count + m;  // slot of the j-th pair, oldest first: (old + j) % m
+      long long base[MAXM];              // its offset in the S and Y stores
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) base[j] = (long long)((old + j) % m) * a.Pmax;
+      float part[2 * MAXM];
+#pragma unroll
+      for (int j = 0; j < 2 * MAXM; ++j) part[j] = 0.f;
+      for (int i = tid; i < P; i += NT) {
+        const float pi = c.p[i];
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+          if (j < count) {
+            part[j] = fmaf(c.S[base[j] + i], pi, part[j]);
+            part[MAXM + j] = fmaf(c.Y[base[j] + i], pi, part[MAXM + j]);
+          }
+      }
+      const unsigned long long cm = (1ull << count) - 1ull;
+      block_sum_many<NT, 2 * MAXM>(part, cm | (cm << MAXM), sh);  // S^T p at j, Y^T p at MAXM + j
+      if (tid == 0) {
+        double t[MAXM], w[MAXM];
+        auto R = [&](int i, int j) { return sh.SY[(old + i) % m][(old + j) % m]; };
+        for (int i = count - 1; i >= 0; --i) {
+          double x = sh.dots[i];
+          for (int j = i + 1; j < count; ++j) x -= R(i, j) * t[j];
+          t[i] = x / R(i, i);
+        }
+        for (int i = 0; i < count; ++i) {
+          double x = R(i, i) * t[i] - gamma * sh.dots[MAXM + i];
+          for (int j = 0; j < count; ++j) x += gamma * sh.YY[(old + i) % m][(old + j) % m] * t[j];
+          w[i] = x;
+        }
+        for (int i = 0; i < count; ++i) {
+          double x = w[i];
+          for (int j = 0; j < i; ++j) x -= R(j, i) * sh.alpha[j];
+          sh.alpha[i] = x / R(i, i);
+          sh.coefS[i] = (float)sh.alpha[i];
+          sh.coefY[i] = (float)(-gamma * t[i]);
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < P; i += NT) {
+        float x = (float)gamma * c.p[i];
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+          if (j < count) x = fmaf(sh.coefS[j], c.S[base[j] + i], fmaf(sh.coefY[j], c.Y[base[j] + i], x));
+        c.p[i] = x;
+      }
     }
     // negate, mask the active set and outward steps at a bound, directional derivative, QN step
     float gpf = 0.f;
     float stepn = 0.f;
-    for (int i = ln; i < P; i += 32) {
+    for (int i = tid; i < P; i += NT) {
       const int t = ptype(c, i);
       const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
       const float gi = c.g[i];
@@ -824,15 +821,15 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       gpf = fmaf(gi, pi, gpf);
       stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
     }
-    double gp = warp_sum((double)gpf);
-    stepn = warp_max(stepn);
+    double gp = block_sum<NT>((double)gpf, sh.red);
+    stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
     if (!(gp < 0.0)) {
       // not a descent direction: restart from the projected steepest descent
       count = 0;
       gamma = 1.0;
       gpf = 0.f;
       stepn = 0.f;
-      for (int i = ln; i < P; i += 32) {
+      for (int i = tid; i < P; i += NT) {
         const int t = ptype(c, i);
         const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
         const float gi = c.g[i];
@@ -843,36 +840,38 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         gpf = fmaf(gi, pi, gpf);
         stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
       }
-      gp = warp_sum((double)gpf);
-      stepn = warp_max(stepn);
+      gp = block_sum<NT>((double)gpf, sh.red);
+      stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
       if (!(gp < 0.0)) {
         status = CSX_FIT_CONVERGED;  // projected gradient vanishes
         break;
       }
     }
-    __syncwarp();
     const bool near_opt = CSX_FIT_NEAR > 0.f && recentres == 0 && stepn <= CSX_FIT_NEAR &&
                           last_step <= CSX_FIT_NEAR;
     const bool at_opt = recentres < 6 && stepn <= 1.f && last_step <= 1.f;
     if (PATH == CSX_PATH_MOMENT && it > 0 && (near_opt || at_opt)) {
-      // The moment form rounds in proportion to the distance from the reference point: at
-      // convergence (and, with CSX_FIT_NEAR > 0, also once the steps first fall within that many
-      // tolerances), move the reference here unless it is already close, so that the last
-      // iterations run on precise values. Each move costs one pass over the pixels.
-      float dref = 0.f;
-      for (int i = ln; i < P; i += 32)
-        dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
-      dref = warp_max(dref);
-      if (dref > 30.f) {
-        for (int i = ln; i < P; i += 32) c.x[i] = c.z[i] / c.hs[i];
-        dnd = cmd(CMD_RECENTRE, dnd);
-        f = cmd(CMD_EVAL, dnd);
-        ++nev;
-        for (int i = ln; i < P; i += 32) c.g[i] = c.gacc[i] / c.hs[i];
-        __syncwarp();
-        ++recentres;
-        --it;  // a move of the reference point is not a quasi-Newton iteration
-        continue;
+      {
+        // The moment form rounds in proportion to the distance from the reference point: at
+        // convergence (and, with CSX_FIT_NEAR > 0, also once the steps first fall within that many
+        // tolerances), move the reference here unless it is already close, so that the last
+        // iterations run on precise values. Each move costs one pass over the pixels.
+        float dref = 0.f;
+        for (int i = tid; i < P; i += NT)
+          dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
+        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
+        if (dref > 30.f) {
+          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
+          __syncthreads();
+          dnd = recentre<NT, NOISE>(a, c, sh, smem);
+          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
+          ++nev;
+          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
+          ++recentres;
+          --it;  // a move of the reference point is not a quasi-Newton iteration
+          __syncthreads();
+          continue;
+        }
       }
     }
     if (it > 0 && stepn <= 1.f && last_step <= 1.f) {
@@ -881,13 +880,13 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     }
     // ---- largest step inside the box --------------------------------------------------
     float amax = 1e30f;
-    for (int i = ln; i < P; i += 32) {
+    for (int i = tid; i < P; i += NT) {
       const int t = ptype(c, i);
       const float pi = c.p[i];
       if (pi < 0.f) amax = fminf(amax, (c.hs[i] * a.lower[t] - c.z[i]) / pi);
       else if (pi > 0.f) amax = fminf(amax, (c.hs[i] * a.upper[t] - c.z[i]) / pi);
     }
-    amax = fmaxf(warp_min(amax), 0.f);
+    amax = fmaxf(block_min<NT>(amax, reinterpret_cast<float*>(sh.red)), 0.f);
     // ---- line search (approximate Wolfe) ------------------------------------------------
     const double eps_f = 1e-6 * fabs(f);
     double alpha = fmin(1.0, (double)amax);
@@ -895,26 +894,25 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
     double ft = 0.0, dnd_t = 0.0;
     bool ok = false;
     for (int ls = 0; ls < a.max_ls && alpha > 0.0; ++ls) {
-      for (int i = ln; i < P; i += 32) {
+      for (int i = tid; i < P; i += NT) {
         const int t = ptype(c, i);
         const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
         const float zi = fminf(fmaxf(c.z[i] + (float)alpha * c.p[i], zl), zu);
         c.zt[i] = zi;
         c.x[i] = zi / c.hs[i];
       }
-      dnd_t = dnd;
-      ft = cmd(CMD_EVAL, dnd_t);
+      __syncthreads();
+      ft = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd_t);
       ++nev;
       if (GMODE == CSX_GRAD_FD) {
-        (void)cmd(CMD_FD_ZT, dnd_t);
+        fd_gradient<NT, NOISE>(a, c, sh, c.zt, c.gt);
         nev += 2 * P;
       } else {
-        for (int i = ln; i < P; i += 32) c.gt[i] = c.gacc[i] / c.hs[i];
+        for (int i = tid; i < P; i += NT) c.gt[i] = c.gacc[i] / c.hs[i];
       }
-      __syncwarp();
       float dphif = 0.f;
-      for (int i = ln; i < P; i += 32) dphif = fmaf(c.gt[i], c.p[i], dphif);
-      const double dphi = warp_sum((double)dphif);
+      for (int i = tid; i < P; i += NT) dphif = fmaf(c.gt[i], c.p[i], dphif);
+      const double dphi = block_sum<NT>((double)dphif, sh.red);
       if (!isfinite(ft) || !isfinite(dphi)) {
         a_hi = alpha;
         d_hi = 1.0;
@@ -951,18 +949,19 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         // Far from the reference point the moment form's rounding can hide the decrease the
         // line search looks for: move the reference here and try again.
         float dref = 0.f;
-        for (int i = ln; i < P; i += 32)
+        for (int i = tid; i < P; i += NT)
           dref = fmaxf(dref, fabsf(c.z[i] / c.hs[i] - c.xr[i]) / a.xtol[ptype(c, i)]);
-        dref = warp_max(dref);
+        dref = block_max<NT>(dref, reinterpret_cast<float*>(sh.red));
         if (dref > 1.f) {
-          for (int i = ln; i < P; i += 32) c.x[i] = c.z[i] / c.hs[i];
-          dnd = cmd(CMD_RECENTRE, dnd);
-          f = cmd(CMD_EVAL, dnd);
+          for (int i = tid; i < P; i += NT) c.x[i] = c.z[i] / c.hs[i];
+          __syncthreads();
+          dnd = recentre<NT, NOISE>(a, c, sh, smem);
+          f = objective<NT, PATH, GMODE, NOISE, false>(a, c, sh, dnd);
           ++nev;
-          for (int i = ln; i < P; i += 32) c.g[i] = c.gacc[i] / c.hs[i];
-          __syncwarp();
+          for (int i = tid; i < P; i += NT) c.g[i] = c.gacc[i] / c.hs[i];
           ++recentres;
           --it;
+          __syncthreads();
           continue;
         }
       }
@@ -975,42 +974,78 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       break;
     }
     // ---- accept: curvature pair and update --------------------------------------------
-    float syf = 0.f, yyf = 0.f;
-    float sn = 0.f;
-    float* Sn = c.S + (long long)head * a.Pmax;
-    float* Yn = c.Y + (long long)head * a.Pmax;
-    for (int i = ln; i < P; i += 32) {
-      const int t = ptype(c, i);
-      const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
-      Sn[i] = si;
-      Yn[i] = yi;
-      syf = fmaf(si, yi, syf);
-      yyf = fmaf(yi, yi, yyf);
-      sn = fmaxf(sn, fabsf(si) / c.hs[i] / a.xtol[t]);
-      c.z[i] = c.zt[i];
-      c.g[i] = c.gt[i];
+    // s = zt - z, y = gt - g; with s^T y, y^T y, and the products of the new pair with the pairs
+    // kept (all but the oldest when the memory is full) for the compact form, in one reduction
+    {
+      const int old = head - count + m;
+      const int j0 = (count == m) ? 1 : 0;  // the oldest pair's slot receives the new pair
+      long long base[MAXM];
+#pragma unroll
+      for (int j = 0; j < MAXM; ++j) base[j] = (long long)((old + j) % m) * a.Pmax;
+      float part[LB_NV];
+#pragma unroll
+      for (int j = 0; j < LB_NV; ++j) part[j] = 0.f;
+      float sn = 0.f;
+      for (int i = tid; i < P; i += NT) {
+        const int t = ptype(c, i);
+        const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
+        part[0] = fmaf(si, yi, part[0]);
+        part[1] = fmaf(yi, yi, part[1]);
+        sn = fmaxf(sn, fabsf(si) / c.hs[i] / a.xtol[t]);
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+          if (j >= j0 && j < count) {
+            const float yk = c.Y[base[j] + i];
+            part[2 + 3 * j] = fmaf(si, yk, part[2 + 3 * j]);
+            part[3 + 3 * j] = fmaf(c.S[base[j] + i], yi, part[3 + 3 * j]);
+            part[4 + 3 * j] = fmaf(yi, yk, part[4 + 3 * j]);
+          }
+      }
+      unsigned long long used = 3ull;
+      for (int j = j0; j < count; ++j) used |= 7ull << (2 + 3 * j);
+      block_sum_many<NT, LB_NV>(part, used, sh);
+      sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
+      const double sy = sh.dots[0], yy = sh.dots[1];
+      const bool keep = sy > 1e-12 * yy && yy > 0.0;
+      float* Sn = c.S + (long long)head * a.Pmax;
+      float* Yn = c.Y + (long long)head * a.Pmax;
+      for (int i = tid; i < P; i += NT) {
+        if (keep) {
+          Sn[i] = c.zt[i] - c.z[i];
+          Yn[i] = c.gt[i] - c.g[i];
+        }
+        c.z[i] = c.zt[i];
+        c.g[i] = c.gt[i];
+      }
+      if (keep && tid == 0) {
+        for (int j = j0; j < count; ++j) {
+          const int k = (old + j) % m;
+          sh.SY[head][k] = sh.dots[2 + 3 * j];
+          sh.SY[k][head] = sh.dots[3 + 3 * j];
+          sh.YY[head][k] = sh.YY[k][head] = sh.dots[4 + 3 * j];
+        }
+        sh.SY[head][head] = sy;
+        sh.YY[head][head] = yy;
+      }
+      last_step = sn;
+      f = ft;
+      if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
+      if (keep) {
+        head = (head + 1) % m;
+        count = min(count + 1, m);
+        gamma = sy / yy;
+      }
     }
-    const double sy = warp_sum((double)syf), yy = warp_sum((double)yyf);
-    sn = warp_max(sn);
-    last_step = sn;
-    f = ft;
-    if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
-    if (sy > 1e-12 * yy && yy > 0.0) {
-      if (ln == 0) sh.rho[head] = 1.0 / sy;
-      head = (head + 1) % m;
-      count = min(count + 1, m);
-      gamma = sy / yy;
-    }
-    __syncwarp();
+    __syncthreads();
   }
-  for (int i = ln; i < P; i += 32) a.beta_out[poff + i] = c.z[i] / c.hs[i];
-  if (ln == 0) {
+  for (int i = tid; i < P; i += NT) a.beta_out[poff + i] = c.z[i] / c.hs[i];
+  if (tid == 0) {
     a.L_out[q] = f - dnd;  // L = chi2_min - sum d^T N d
     a.status[q] = status;
     a.iters[q] = it;
     if (a.nevals) a.nevals[q] = nev;
   }
-  (void)cmd(CMD_DONE, dnd);
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------------- AdaTopK --------------
@@ -1067,7 +1102,7 @@ __device__ void fit_problem_adatopk(const FitArgs& a, Ctx& c, Shared& sh, float*
   __syncthreads();
   double dnd = 0.0;
   int recentres = 0;
-  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem);
+  if (PATH == CSX_PATH_MOMENT) dnd = recentre<NT, NOISE>(a, c, sh, smem, false);
   double f = objective<NT, PATH, CSX_GRAD_ADJOINT, NOISE, false>(a, c, sh, dnd);
   int nev = 1, status = CSX_FIT_MAXITER, it = 0;
   if (!isfinite(f)) {
@@ -1411,8 +1446,8 @@ int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path
 
 template <int NT, int PATH>
 constexpr size_t fit_dyn_smem() {
-  // moment path: build staging (32 pixel rows per warp) or, during evaluations, 30 (+ 171) floats
-  // per thread followed by the warp partials; streaming path: the warp partials
+  // moment path: build staging (32 pixel rows per warp) or, during evaluations, 30 floats per
+  // thread followed by the warp partials; streaming path: the warp partials
   constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
   constexpr size_t eval = (size_t)fit_rows_floats<NT, PATH>() + (size_t)(NT / 32) * SMEM_P;
   if (PATH != CSX_PATH_MOMENT) return eval * sizeof(float);

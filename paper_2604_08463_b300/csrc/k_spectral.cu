@@ -3,6 +3,8 @@
 #include "csx_host.h"
 #include "csx_tma.cuh"
 
+#include <atomic>
+
 namespace csx {
 
 // Count of bounded waits that gave up (a tensor copy that did not arrive within the bound) since the
@@ -110,17 +112,10 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 // L with NaN. Waits are bounded (about 2 s): on time-out the CTA waits (bounded) for its copies
 // still in flight, poisons L with NaN and returns.
 // ---------------------------------------------------------------------------------------------
-// Build-time tuning switches (the defaults are the measured best on B300): pixels (= threads) per
-// tile, pipeline stages, and the minimum resident CTAs per SM asked of ptxas.
-#ifndef CSX_TS_NT
-#define CSX_TS_NT 128
-#endif
-#ifndef CSX_TS_S
-#define CSX_TS_S 2
-#endif
-#ifndef CSX_TS_MINB
-#define CSX_TS_MINB (512 / CSX_TS_NT)
-#endif
+// Tile schedule: pixels (= threads) per tile NT and pipeline stages S are template parameters; the
+// schedule of a launch is the one selected with set_stream_schedule (csx_stream_schedule), default
+// (128, 2), the measured best on the full-sky nside-64 case; resident CTAs per SM asked of ptxas:
+// 512 / NT. Build-time switches of the algorithm (the defaults are the measured best on B300):
 #ifndef CSX_TS_WARPRUNS
 #define CSX_TS_WARPRUNS 1  // 1: each warp forms the scalars of its own runs (no block-wide table)
 #endif
@@ -133,18 +128,14 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 #ifndef CSX_TS_GRADVEC
 #define CSX_TS_GRADVEC 0  // 1: the gradient kernel also evaluates pixels from the run vectors
 #endif
-constexpr int TS_NT = CSX_TS_NT;                    // threads = pixels per tile
-constexpr int TS_NW = TS_NT / 32;
-constexpr int TS_S = CSX_TS_S;                      // pipeline stages
 constexpr long long TS_WAIT_CYCLES = 4000000000LL;  // bound of one wait, in SM clock cycles
 constexpr int TS_RUNVEC = 32;  // runs per tile whose band vectors are kept in the run table
 constexpr bool TS_GRADVEC = CSX_TS_GRADVEC != 0;
 constexpr bool TS_WARPRUNS = CSX_TS_WARPRUNS != 0;
 constexpr bool TS_CONTIG = CSX_TS_CONTIG != 0;
 constexpr bool TS_RUNCACHE = CSX_TS_RUNCACHE != 0;
-constexpr int TS_RUNVEC_W = TS_RUNVEC / (CSX_TS_NT / 32);  // run vectors per warp
 
-template <int NOISE>
+template <int NOISE, int TS_NT, int TS_S>
 struct TsShape {
   static constexpr bool RUNS = NOISE != CSX_NOISE_PERPIXEL;
   static constexpr int DB = TS_NT * 128;                                 // d: [TS_NT][2][16] floats
@@ -156,11 +147,13 @@ struct TsShape {
   }
 };
 
-template <int NOISE, bool GRAD, bool SMEM_GRAD>
-__global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
+template <int NOISE, bool GRAD, bool SMEM_GRAD, int TS_NT, int TS_S>
+__global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     k_spectral_tma(const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap mn,
                    const SpecArgs a) {
-  using Sh = TsShape<NOISE>;
+  constexpr int TS_NW = TS_NT / 32;
+  constexpr int TS_RUNVEC_W = TS_RUNVEC / TS_NW;  // run vectors per warp
+  using Sh = TsShape<NOISE, TS_NT, TS_S>;
   extern __shared__ __align__(16) unsigned char ts_smem[];
   __shared__ __align__(8) uint64_t full[TS_S];
   __shared__ double sred[TS_NW];
@@ -408,32 +401,33 @@ __global__ void __launch_bounds__(TS_NT, CSX_TS_MINB)
   }
 }
 
-template <int NOISE, bool GRAD, bool SMEM_GRAD>
+template <int NOISE, bool GRAD, bool SMEM_GRAD, int NT, int S>
 static int launch_tma_one(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, dim3 grid,
                           cudaStream_t s) {
-  const size_t smem = TsShape<NOISE>::smem(a.P, GRAD && SMEM_GRAD);
+  using Sh = TsShape<NOISE, NT, S>;
+  const size_t smem = Sh::smem(a.P, GRAD && SMEM_GRAD);
   // the attribute covers the ring plus a P-vector of up to 16384 floats
-  CSX_CUDA(cudaFuncSetAttribute(k_spectral_tma<NOISE, GRAD, SMEM_GRAD>,
+  CSX_CUDA(cudaFuncSetAttribute(k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)TsShape<NOISE>::smem(16384, true)));
-  k_spectral_tma<NOISE, GRAD, SMEM_GRAD><<<grid, TS_NT, smem, s>>>(md, mn, a);
+                                (int)Sh::smem(16384, true)));
+  k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S><<<grid, NT, smem, s>>>(md, mn, a);
   CSX_CUDA(cudaGetLastError());
   return CSX_OK;
 }
 
-template <int NOISE>
+template <int NOISE, int NT, int S>
 static int launch_tma(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, bool grad,
                       dim3 grid, cudaStream_t s) {
-  if (!grad) return launch_tma_one<NOISE, false, false>(md, mn, a, grid, s);
-  if (a.P <= 16384) return launch_tma_one<NOISE, true, true>(md, mn, a, grid, s);
-  return launch_tma_one<NOISE, true, false>(md, mn, a, grid, s);
+  if (!grad) return launch_tma_one<NOISE, false, false, NT, S>(md, mn, a, grid, s);
+  if (a.P <= 16384) return launch_tma_one<NOISE, true, true, NT, S>(md, mn, a, grid, s);
+  return launch_tma_one<NOISE, true, false, NT, S>(md, mn, a, grid, s);
 }
 
 // Tensor maps of one launch: d as [problems][npix][32 floats] (box 32 x 256 x 1, 128-byte
 // swizzle) and, for per-pixel noise, N^-1 as [npix][16 floats] (box 16 x 256, 64-byte swizzle).
 // Returns false if the encoder is unavailable or refuses (the entry points have already checked
 // that d and N^-1 are 16-byte aligned).
-static bool make_maps(const SpecArgs& a, CUtensorMap* md, CUtensorMap* mn) {
+static bool make_maps(const SpecArgs& a, CUtensorMap* md, CUtensorMap* mn, int TS_NT) {
   if ((reinterpret_cast<uintptr_t>(a.d) & 15) != 0) return false;
   {
     const cuuint64_t dims[3] = {2 * NB, (cuuint64_t)a.npix, (cuuint64_t)a.nprob};
@@ -459,16 +453,53 @@ static bool make_maps(const SpecArgs& a, CUtensorMap* md, CUtensorMap* mn) {
 
 // Tiles per CTA of the TMA kernel: up to 2048 pixels' worth, fewer when that would leave under
 // 4 CTAs per resident CTA slot.
-static int tma_grid_x(int npix, int nprob) {
+static int tma_grid_x(int npix, int nprob, int TS_NT) {
   const long long ntile = (npix + TS_NT - 1) / TS_NT;
-  long long tpc = ntile * nprob / (148LL * CSX_TS_MINB * 4);
+  long long tpc = ntile * nprob / (148LL * (512 / TS_NT) * 4);
   const long long tmax = 2048 / TS_NT;
   tpc = tpc < 1 ? 1 : (tpc > tmax ? tmax : tpc);
   return (int)((ntile + tpc - 1) / tpc);
 }
 
+// The schedules the streaming kernel is built for: (pixels per tile, stages).
+constexpr int TS_SCHED[][2] = {{128, 2}, {64, 2}, {64, 3}, {128, 3}, {128, 4}, {256, 2}};
+constexpr int TS_NSCHED = sizeof(TS_SCHED) / sizeof(TS_SCHED[0]);
+static std::atomic<int> g_sched{0};
+
+int set_stream_schedule(int tile, int stages) {
+  if (tile == 0 && stages == 0) {
+    g_sched.store(0);
+    return CSX_OK;
+  }
+  for (int i = 0; i < TS_NSCHED; ++i)
+    if (TS_SCHED[i][0] == tile && TS_SCHED[i][1] == stages) {
+      g_sched.store(i);
+      return CSX_OK;
+    }
+  return fail(CSX_EINVAL, "unsupported streaming schedule (tile, stages)");
+}
+
+void get_stream_schedule(int* tile, int* stages) {
+  const int i = g_sched.load();
+  *tile = TS_SCHED[i][0];
+  *stages = TS_SCHED[i][1];
+}
+
+template <int NT, int S>
+static int launch_sched(const SpecArgs& b, bool grad, cudaStream_t s) {
+  CUtensorMap md, mn;
+  if (!make_maps(b, &md, &mn, NT)) return fail(CSX_ECUDA, "tensor-map encoding failed (cuTensorMapEncodeTiled)");
+  const dim3 grid(tma_grid_x(b.npix, b.nprob, NT), b.nprob);
+  switch (b.noise_kind) {
+    case CSX_NOISE_HOMOGENEOUS: return launch_tma<CSX_NOISE_HOMOGENEOUS, NT, S>(md, mn, b, grad, grid, s);
+    case CSX_NOISE_SEPARABLE: return launch_tma<CSX_NOISE_SEPARABLE, NT, S>(md, mn, b, grad, grid, s);
+    default: return launch_tma<CSX_NOISE_PERPIXEL, NT, S>(md, mn, b, grad, grid, s);
+  }
+}
+
 int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s) {
   if (a.nprob == 0 || a.npix == 0) return CSX_OK;
+  const int sched = g_sched.load();
   // at most 65535 problems per launch (grid.y limit)
   for (int q0 = 0; q0 < a.nprob; q0 += 65535) {
     SpecArgs b = a;
@@ -479,17 +510,14 @@ int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s) {
     b.beta = a.beta + (long long)q0 * a.P;
     b.L = a.L + q0;
     b.grad = a.grad ? a.grad + (long long)q0 * a.P : nullptr;
-    CUtensorMap md, mn;
     int rc;
-    if (make_maps(b, &md, &mn)) {
-      const dim3 grid(tma_grid_x(b.npix, nq), nq);
-      switch (b.noise_kind) {
-        case CSX_NOISE_HOMOGENEOUS: rc = launch_tma<CSX_NOISE_HOMOGENEOUS>(md, mn, b, grad, grid, s); break;
-        case CSX_NOISE_SEPARABLE: rc = launch_tma<CSX_NOISE_SEPARABLE>(md, mn, b, grad, grid, s); break;
-        default: rc = launch_tma<CSX_NOISE_PERPIXEL>(md, mn, b, grad, grid, s); break;
-      }
-    } else {
-      return fail(CSX_ECUDA, "tensor-map encoding failed (cuTensorMapEncodeTiled)");
+    switch (sched) {
+      case 1: rc = launch_sched<64, 2>(b, grad, s); break;
+      case 2: rc = launch_sched<64, 3>(b, grad, s); break;
+      case 3: rc = launch_sched<128, 3>(b, grad, s); break;
+      case 4: rc = launch_sched<128, 4>(b, grad, s); break;
+      case 5: rc = launch_sched<256, 2>(b, grad, s); break;
+      default: rc = launch_sched<128, 2>(b, grad, s); break;
     }
     if (rc) return rc;
   }

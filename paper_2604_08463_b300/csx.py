@@ -23,7 +23,7 @@ STATUS = {0: "converged", 1: "max_iter", 2: "nonphysical", 3: "line_search", 4: 
 M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_device_status",
-           "csx_fit_defaults", "csx_mixing",
+           "csx_stream_schedule", "csx_fit_defaults", "csx_mixing",
            "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_f64",
            "csx_spectral_grad_noalloc",
            "csx_cell_like_grad", "csx_build_cells", "csx_fit_batch", "csx_reconstruct",
@@ -70,6 +70,7 @@ def lib():
         L.csx_last_error.restype = ctypes.c_char_p
         L.csx_release.restype = i32
         L.csx_device_status.argtypes = [vp]
+        L.csx_stream_schedule.argtypes = [i32, i32, pi32]
         L.csx_fit_defaults.argtypes = [POINTER(CFitOpts)]
         L.csx_mixing.argtypes = [POINTER(CModel), i32, vp, vp, vp, vp]
         L.csx_spectral_like.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp, vp]
@@ -184,6 +185,19 @@ def version():
 
 def release():
     _check(lib().csx_release())
+
+
+STREAM_SCHEDULES = ((128, 2), (64, 2), (64, 3), (128, 3), (128, 4), (256, 2))
+
+
+def stream_schedule(tile=None, stages=None):
+    """Select the streaming kernel's (pixels per tile, stages) for the calls that follow (None: keep
+    the current one; (0, 0): the default); returns the schedule in force as a tuple."""
+    cur = (c_int32 * 2)()
+    t = -1 if tile is None else int(tile)
+    st = -1 if stages is None else int(stages)
+    _check(lib().csx_stream_schedule(t, st, cur))
+    return int(cur[0]), int(cur[1])
 
 
 def device_status():

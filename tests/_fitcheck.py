@@ -45,7 +45,8 @@ def sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=None):
     tolerance is accepted as another correct optimum only when the oracle's own FP64 likelihood at
     the fitted point is no worse than at its optimum by more than eps = 1e-6 chi2_min (an equally
     good point of a flat or multi-modal likelihood), and the oracle's curvature there is positive.
-    Such parameters are counted, printed and bounded by `max_alternative`.
+    Such parameters are counted, printed and bounded by `max_alternative` (a count, or a fraction
+    of the interior parameters checked when below 1).
     Returns (worst |err|/tol over the interior parameters, parameters accepted as alternatives)."""
     from oracle import likelihood as lk
     wl = case.wl
@@ -59,7 +60,7 @@ def sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=None):
         with oracle_pool(min(len(jobs), 8)) as pool:
             refs = pool.map(fit_job, jobs)
     out = {k: v.cpu().numpy() for k, v in res.items()}
-    worst, alternative = 0.0, 0
+    worst, alternative, checked = 0.0, 0, 0
     for q, (x_ref, L_ref, interior) in zip(picks, refs):
         c, r = divmod(q, wl.nreal)
         K = wl.K[c]
@@ -70,6 +71,7 @@ def sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=None):
         tol = TOL_BETA[types]
         err = np.abs(got - x_ref)
         assert abs(out["L"][q] - L_ref) <= 1e-5 * abs(L_ref), (q, out["L"][q], L_ref)
+        checked += int(interior.sum())
         over = np.nonzero(interior & (err > tol))[0]
         if over.size:
             d64, lab = case.d64(r), wl.labels[c]
@@ -84,7 +86,10 @@ def sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=None):
                 assert ok, (q, i, err[i] / tol[i], L_at - L_ref, eps)
                 alternative += 1
         worst = max(worst, (err / tol)[interior].max(initial=0.0))
-    print("worst |err|/tol %.3f; parameters accepted as alternative optima: %d (at most %d)"
-          % (worst, alternative, max_alternative))
-    assert alternative <= max_alternative, (alternative, max_alternative)
+    bound = max_alternative
+    if 0 < max_alternative < 1:
+        bound = int(np.floor(max_alternative * checked))
+    print("worst |err|/tol %.3f; parameters accepted as alternative optima: %d of %d checked "
+          "(at most %d)" % (worst, alternative, checked, bound))
+    assert alternative <= bound, (alternative, bound)
     return worst, alternative

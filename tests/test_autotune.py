@@ -50,3 +50,38 @@ def test_first_candidate_kept_within_the_margin():
     t["moment/64"] = 90.0
     opts, _ = at.choose("m", at.candidates("separable"), lambda p, n: t["%s/%d" % (p, n)])
     assert opts == {"path": "moment", "threads": 64}
+
+
+def test_stream_schedule_choice_and_cache(tmp_path):
+    from paper_2604_08463_b300 import csx
+    cache = str(tmp_path / "tune.json")
+    key = at.stream_key("separable", 49152, 100, 150, True)
+    assert key != at.stream_key("separable", 49152, 100, 150, False)
+    assert key == at.stream_key("separable", 50000, 100, 160, True)
+    t = {"128/2": 10.0, "64/2": 9.8, "64/3": 12.0, "128/3": 9.0, "128/4": 9.5, "256/2": 11.0}
+    calls = []
+
+    def timer(tile, stages):
+        calls.append((tile, stages))
+        return t["%d/%d" % (tile, stages)]
+
+    sched, e = at.choose_schedule(key, list(csx.STREAM_SCHEDULES), timer, cache)
+    assert sched == (128, 3) and len(calls) == 6 and e["ms"]["256/2"] == 11.0
+    sched2, _ = at.choose_schedule(key, list(csx.STREAM_SCHEDULES), timer, cache)
+    assert sched2 == (128, 3) and len(calls) == 6
+    t["128/3"], t["128/4"] = 9.9, 9.75  # all within the 3% margin of the default
+    sched3, _ = at.choose_schedule("other", list(csx.STREAM_SCHEDULES), timer, None)
+    assert sched3 == (128, 2)
+
+
+def test_stream_schedule_setter_is_host_only():
+    from paper_2604_08463_b300 import build, csx
+    build.build()
+    assert csx.stream_schedule() == (128, 2)
+    assert csx.stream_schedule(256, 2) == (256, 2)
+    assert csx.stream_schedule() == (256, 2)
+    assert csx.stream_schedule(0, 0) == (128, 2)
+    import pytest
+    with pytest.raises(csx.CsxError):
+        csx.stream_schedule(96, 2)
+    assert csx.stream_schedule() == (128, 2)

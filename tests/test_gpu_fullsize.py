@@ -158,7 +158,9 @@ def test_large_k_scan_nside16_sampled_problems(csx):
     P = np.repeat(wl.P, wl.nreal)
     picks, refs = stored_refs("scan16_k1000", case)
     print("P", P[picks])
-    _sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=refs)
+    # patches of one or two pixels at nside 16 leave some beta_s flat to ~1e-9 of chi2: up to 1% of
+    # the parameters may sit at another optimum as good in FP64 (within 1e-6 chi2)
+    _sampled_fit_check(csx, case, res, picks, max_alternative=0.01, refs=refs)
 
 
 def test_cell_moment_evaluation_nside64_scan(csx):
