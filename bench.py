@@ -405,12 +405,21 @@ def run_csx(args):
                "L_minus_lbfgs": {"median": float(np.median(dL)), "max": float(dL.max()),
                                  "frac_lower": float((dL < 0).mean())}}
 
-    streaming = streaming_rates(csx, hbm) if (rank == 0 and not args.no_stream) else None
-    fullsky = fullsky_fit_rates(csx) if (rank == 0 and not args.no_fullsky) else None
-    pipeline = pipeline_rates(csx) if (rank == 0 and not args.no_pipeline) else None
-    kmeans_gpu = kmeans_rates(csx, inp) if (rank == 0 and not args.no_kmeans) else None
-    spectra = (spectra_rates(csx, inp, model, sky, labels, fg, res["beta"])
-               if (rank == 0 and not args.no_spectra) else None)
+    def leg(enabled, fn, *a):
+        """A side measurement; an error in one is recorded in its key, not raised."""
+        if rank != 0 or not enabled:
+            return None
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001
+            torch.cuda.synchronize()
+            return {"error": "%s: %s" % (type(e).__name__, e)}
+
+    streaming = leg(not args.no_stream, streaming_rates, csx, hbm)
+    fullsky = leg(not args.no_fullsky, fullsky_fit_rates, csx)
+    pipeline = leg(not args.no_pipeline, pipeline_rates, csx)
+    kmeans_gpu = leg(not args.no_kmeans, kmeans_rates, csx, inp)
+    spectra = leg(not args.no_spectra, spectra_rates, csx, inp, model, sky, labels, fg, res["beta"])
 
     # end to end: pinned host inputs -> device, step, results -> host
     e2e = None

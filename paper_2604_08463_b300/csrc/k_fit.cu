@@ -35,7 +35,7 @@ namespace csx {
 #define CSX_FIT_NEAR 0.f
 #endif
 #ifndef CSX_FIT_MIN_BLOCKS
-#define CSX_FIT_MIN_BLOCKS 4
+#define CSX_FIT_MIN_BLOCKS 3
 #endif
 
 constexpr int SMEM_P = 1024;   // parameter vectors up to this length accumulate in shared memory
@@ -54,48 +54,12 @@ struct Ctx {
   float* smem;        // moment path: dynamic shared memory (build staging, then per-thread rows)
 };
 
-constexpr int LB_NV = 2 + 3 * MAXM;  // dot products fused into one reduction at a step's acceptance
-
 struct Shared {
   double red[16];
   double rho[MAXM], alpha[MAXM];
   float gacc[SMEM_P], hacc[SMEM_P];
   float stage[8][32];  // per-warp staging of warp_run_accum3
-  // compact L-BFGS: s_i^T y_j and y_i^T y_j of the stored pairs (by slot), the direction's
-  // coefficients, and the per-warp partial sums of the fused dot products
-  double SY[MAXM][MAXM], YY[MAXM][MAXM];
-  float coefS[MAXM], coefY[MAXM];
-  double wpart[8][LB_NV];
-  double dots[LB_NV];
 };
-
-// Sums over the block of the per-thread FP32 partials part[v] whose bit v is set in `used`,
-// deterministic: a fixed shuffle tree in each warp, then the warps' sums in warp order in FP64
-// (thread v adds value v); one barrier pair for all of them. Totals in sh.dots[v].
-template <int NT, int NV>
-__device__ __forceinline__ void block_sum_many(float (&part)[NV], unsigned long long used,
-                                               Shared& sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if ((used >> v) & 1ull) {
-      float x = part[v];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) sh.wpart[warp][v] = (double)x;
-    }
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < NV; v += NT) {
-    if ((used >> v) & 1ull) {
-      double t = 0.0;
-#pragma unroll
-      for (int w = 0; w < NT / 32; ++w) t += sh.wpart[w][v];
-      sh.dots[v] = t;
-    }
-  }
-  __syncthreads();
-}
 
 // Gradient (and Gauss-Newton diagonal) accumulation without float atomics: each warp adds its
 // run totals to its own partial P-vector in program order (warp_run_accum3), and the vectors are
@@ -134,10 +98,37 @@ __device__ __forceinline__ int ptype(const Ctx& c, int i) {
 }
 
 // ------------------------------------------------------------------------------ tables ----------
+// The rows of table_entry; a dust-temperature patch's B and dlnB/dT entries of a band are formed by
+// one thread from the same two expm1 values: with E = e^x - 1, x / (1 - e^-x) = x (1 + E) / E.
 template <int NT>
 __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, float* tab) {
-  const int n = c.rows * NB;
-  for (int i = threadIdx.x; i < n; i += NT) tab[i] = table_entry(a.bands, i >> 4, i & 15, c.Kd, c.KT, x);
+  const int nd = c.Kd * NB, nt = c.KT * NB, n = nd + nt + c.Ks * NB;
+  const Bands& b = a.bands;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const int f = i & 15;
+    if (i < nd) {
+      tab[i] = table_entry(b, i >> 4, f, c.Kd, c.KT, x);
+    } else if (i < nd + nt) {
+      const int j = (i - nd) >> 4;
+      const float T = x[c.Kd + j];
+      float vb = 0.f, vd = 0.f;
+      if (f < b.nf) {
+        if (T > 0.f) {
+          const float x0 = b.xk0 / T, xf = b.xk[f] / T;
+          const float E0 = expm1f(x0), Ef = expm1f(xf);
+          vb = b.cd[f] * E0 / Ef;
+          vd = (xf * (1.f + Ef) / Ef - x0 * (1.f + E0) / E0) / T;
+        } else {
+          vb = vd = nan_f();
+        }
+      }
+      tab[(c.Kd + j) * NB + f] = vb;
+      tab[(c.Kd + c.KT + j) * NB + f] = vd;
+    } else {
+      const int r = c.Kd + 2 * c.KT + ((i - nd - nt) >> 4);
+      tab[r * NB + f] = table_entry(b, r, f, c.Kd, c.KT, x);
+    }
+  }
   __syncthreads();
 }
 
@@ -746,11 +737,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
   float last_step = 1e30f;
   const double delta = 0.1, sigma = 0.9;
   for (it = 0; it < a.max_iter; ++it) {
-    // ---- direction: L-BFGS inverse Hessian times the free-set gradient ----------------------
-    // compact form (Byrd, Nocedal and Schnabel 1994), the same product as the two-loop recursion:
-    //   H p = gamma p + S a - gamma Y t,  t = R^-1 S^T p,  a = R^-T ((D + gamma Y^T Y) t - gamma Y^T p)
-    // with S, Y the stored pairs oldest first, R the upper triangle of S^T Y and D its diagonal;
-    // the 2 count dot products S^T p, Y^T p are formed in one pass and one block reduction.
+    // ---- direction: two-loop recursion on the free-set gradient --------------------------
     for (int i = tid; i < P; i += NT) {
       const int t = ptype(c, i);
       const float zl = c.hs[i] * a.lower[t], zu = c.hs[i] * a.upper[t];
@@ -758,54 +745,28 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       const bool act = (c.z[i] <= zl && gi > 0.f) || (c.z[i] >= zu && gi < 0.f);
       c.p[i] = act ? 0.f : gi;
     }
-    if (count > 0) {
-      const int old = head - count + m;  // slot of the j-th pair, oldest first: (old + j) % m
-      long long base[MAXM];              // its offset in the S and Y stores
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j) base[j] = (long long)((old + j) % m) * a.Pmax;
-      float part[2 * MAXM];
-#pragma unroll
-      for (int j = 0; j < 2 * MAXM; ++j) part[j] = 0.f;
-      for (int i = tid; i < P; i += NT) {
-        const float pi = c.p[i];
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-          if (j < count) {
-            part[j] = fmaf(c.S[base[j] + i], pi, part[j]);
-            part[MAXM + j] = fmaf(c.Y[base[j] + i], pi, part[MAXM + j]);
-          }
-      }
-      const unsigned long long cm = (1ull << count) - 1ull;
-      block_sum_many<NT, 2 * MAXM>(part, cm | (cm << MAXM), sh);  // S^T p at j, Y^T p at MAXM + j
-      if (tid == 0) {
-        double t[MAXM], w[MAXM];
-        auto R = [&](int i, int j) { return sh.SY[(old + i) % m][(old + j) % m]; };
-        for (int i = count - 1; i >= 0; --i) {
-          double x = sh.dots[i];
-          for (int j = i + 1; j < count; ++j) x -= R(i, j) * t[j];
-          t[i] = x / R(i, i);
-        }
-        for (int i = 0; i < count; ++i) {
-          double x = R(i, i) * t[i] - gamma * sh.dots[MAXM + i];
-          for (int j = 0; j < count; ++j) x += gamma * sh.YY[(old + i) % m][(old + j) % m] * t[j];
-          w[i] = x;
-        }
-        for (int i = 0; i < count; ++i) {
-          double x = w[i];
-          for (int j = 0; j < i; ++j) x -= R(j, i) * sh.alpha[j];
-          sh.alpha[i] = x / R(i, i);
-          sh.coefS[i] = (float)sh.alpha[i];
-          sh.coefY[i] = (float)(-gamma * t[i]);
-        }
-      }
-      __syncthreads();
-      for (int i = tid; i < P; i += NT) {
-        float x = (float)gamma * c.p[i];
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-          if (j < count) x = fmaf(sh.coefS[j], c.S[base[j] + i], fmaf(sh.coefY[j], c.Y[base[j] + i], x));
-        c.p[i] = x;
-      }
+    for (int j = 0; j < count; ++j) {
+      const int k = (head - 1 - j + m) % m;
+      const float* Sk = c.S + (long long)k * a.Pmax;
+      float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
+      for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
+      const double dot = block_sum<NT>((double)dotf, sh.red);
+      const double al = sh.rho[k] * dot;
+      if (tid == 0) sh.alpha[k] = al;
+      const float* Yk = c.Y + (long long)k * a.Pmax;
+      for (int i = tid; i < P; i += NT) c.p[i] -= (float)al * Yk[i];
+    }
+    for (int i = tid; i < P; i += NT) c.p[i] *= (float)gamma;
+    for (int j = count - 1; j >= 0; --j) {
+      const int k = (head - 1 - j + m) % m;
+      const float* Yk = c.Y + (long long)k * a.Pmax;
+      float dotf = 0.f;
+      for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
+      const double dot = block_sum<NT>((double)dotf, sh.red);
+      const double be = sh.rho[k] * dot;
+      const float* Sk = c.S + (long long)k * a.Pmax;
+      const float coef = (float)(sh.alpha[k] - be);
+      for (int i = tid; i < P; i += NT) c.p[i] += coef * Sk[i];
     }
     // negate, mask the active set and outward steps at a bound, directional derivative, QN step
     float gpf = 0.f;
@@ -974,67 +935,32 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       break;
     }
     // ---- accept: curvature pair and update --------------------------------------------
-    // s = zt - z, y = gt - g; with s^T y, y^T y, and the products of the new pair with the pairs
-    // kept (all but the oldest when the memory is full) for the compact form, in one reduction
-    {
-      const int old = head - count + m;
-      const int j0 = (count == m) ? 1 : 0;  // the oldest pair's slot receives the new pair
-      long long base[MAXM];
-#pragma unroll
-      for (int j = 0; j < MAXM; ++j) base[j] = (long long)((old + j) % m) * a.Pmax;
-      float part[LB_NV];
-#pragma unroll
-      for (int j = 0; j < LB_NV; ++j) part[j] = 0.f;
-      float sn = 0.f;
-      for (int i = tid; i < P; i += NT) {
-        const int t = ptype(c, i);
-        const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
-        part[0] = fmaf(si, yi, part[0]);
-        part[1] = fmaf(yi, yi, part[1]);
-        sn = fmaxf(sn, fabsf(si) / c.hs[i] / a.xtol[t]);
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-          if (j >= j0 && j < count) {
-            const float yk = c.Y[base[j] + i];
-            part[2 + 3 * j] = fmaf(si, yk, part[2 + 3 * j]);
-            part[3 + 3 * j] = fmaf(c.S[base[j] + i], yi, part[3 + 3 * j]);
-            part[4 + 3 * j] = fmaf(yi, yk, part[4 + 3 * j]);
-          }
-      }
-      unsigned long long used = 3ull;
-      for (int j = j0; j < count; ++j) used |= 7ull << (2 + 3 * j);
-      block_sum_many<NT, LB_NV>(part, used, sh);
-      sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
-      const double sy = sh.dots[0], yy = sh.dots[1];
-      const bool keep = sy > 1e-12 * yy && yy > 0.0;
-      float* Sn = c.S + (long long)head * a.Pmax;
-      float* Yn = c.Y + (long long)head * a.Pmax;
-      for (int i = tid; i < P; i += NT) {
-        if (keep) {
-          Sn[i] = c.zt[i] - c.z[i];
-          Yn[i] = c.gt[i] - c.g[i];
-        }
-        c.z[i] = c.zt[i];
-        c.g[i] = c.gt[i];
-      }
-      if (keep && tid == 0) {
-        for (int j = j0; j < count; ++j) {
-          const int k = (old + j) % m;
-          sh.SY[head][k] = sh.dots[2 + 3 * j];
-          sh.SY[k][head] = sh.dots[3 + 3 * j];
-          sh.YY[head][k] = sh.YY[k][head] = sh.dots[4 + 3 * j];
-        }
-        sh.SY[head][head] = sy;
-        sh.YY[head][head] = yy;
-      }
-      last_step = sn;
-      f = ft;
-      if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
-      if (keep) {
-        head = (head + 1) % m;
-        count = min(count + 1, m);
-        gamma = sy / yy;
-      }
+    float syf = 0.f, yyf = 0.f;
+    float sn = 0.f;
+    float* Sn = c.S + (long long)head * a.Pmax;
+    float* Yn = c.Y + (long long)head * a.Pmax;
+    for (int i = tid; i < P; i += NT) {
+      const int t = ptype(c, i);
+      const float si = c.zt[i] - c.z[i], yi = c.gt[i] - c.g[i];
+      Sn[i] = si;
+      Yn[i] = yi;
+      syf = fmaf(si, yi, syf);
+      yyf = fmaf(yi, yi, yyf);
+      sn = fmaxf(sn, fabsf(si) / c.hs[i] / a.xtol[t]);
+      c.z[i] = c.zt[i];
+      c.g[i] = c.gt[i];
+    }
+    double sy = syf, yy = yyf;
+    block_sum2<NT>(sy, yy, sh.red);
+    sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
+    last_step = sn;
+    f = ft;
+    if (PATH != CSX_PATH_MOMENT) dnd = dnd_t;
+    if (sy > 1e-12 * yy && yy > 0.0) {
+      if (tid == 0) sh.rho[head] = 1.0 / sy;
+      head = (head + 1) % m;
+      count = min(count + 1, m);
+      gamma = sy / yy;
     }
     __syncthreads();
   }
