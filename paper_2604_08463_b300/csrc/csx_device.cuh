@@ -269,6 +269,15 @@ __device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Prefetch of the global line holding p into L1.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
+}
+// Asynchronous prefetch of a global range into L2 (nothing to wait for): p 16-byte aligned, bytes
+// a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // ---------------------------------------------------------------------------------------------
 // Scatter-add of per-lane values into acc[key], combined over runs of equal keys in consecutive
@@ -392,6 +401,40 @@ __device__ __forceinline__ T block_sum(T v, T* sbuf) {
   __syncthreads();
   T t = ((threadIdx.x & 31) < NT / 32) ? sbuf[threadIdx.x & 31] : T(0);
   return warp_sum(t);
+}
+
+// Sum of FP32 per-thread partials: FP32 within each warp, FP64 across the warps (NT / 32 - 1
+// additions, read from shared memory by every thread), the same value in every thread.
+template <int NT>
+__device__ __forceinline__ double block_sum_f(float v, double* sbuf) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = (double)v;
+  __syncthreads();
+  double t = sbuf[0];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) t += sbuf[w];
+  return t;
+}
+
+// Two block_sum_f at once (one pair of barriers); sbuf holds 2 NT / 32 doubles.
+template <int NT>
+__device__ __forceinline__ void block_sum2_f(float a, float b, double* sbuf, double& ra, double& rb) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    sbuf[threadIdx.x >> 5] = (double)a;
+    sbuf[NT / 32 + (threadIdx.x >> 5)] = (double)b;
+  }
+  __syncthreads();
+  ra = sbuf[0];
+  rb = sbuf[NT / 32];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) {
+    ra += sbuf[w];
+    rb += sbuf[NT / 32 + w];
+  }
 }
 
 // Two sums at once (one pair of barriers).

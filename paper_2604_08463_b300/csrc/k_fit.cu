@@ -137,8 +137,11 @@ __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, floa
 // with A_r the cell's mixing matrix at beta_ref:
 //   s = (A_r^T N A_r)^-1 A_r^T N d,   r = d - A_r s,   v = [r_0 .. r_14, s_0, s_1, s_2]
 // and per cell M_c = sum_p w_p sum_s v v^T (18 x 18): its blocks are R = sum w r r^T,
-// C = sum w r s^T and Q = sum w s s^T. Stored as the upper triangle, entry-major:
-//   mom[e(i,j) * ncell + cell],  e(i,j) = i (35 - i) / 2 + j,  0 <= i <= j < 18   (171 entries).
+// C = sum w r s^T and Q = sum w s s^T. Stored as the upper triangle, entry-major within groups of
+// 32 consecutive cells (one 128-byte row per entry and group, so the warp that evaluates a group
+// reads one line per entry at a compile-time offset):
+//   mom[((cell / 32) * 171 + e(i,j)) * 32 + cell % 32],  e(i,j) = i (35 - i) / 2 + j,
+//   0 <= i <= j < 18   (171 entries).
 // Since d = A_r s + r exactly, S_c = sum w d d^T = A_r Q A_r^T + A_r C^T + C A_r^T + R, but every stored
 // block is small where it has to be: R and C carry residuals, not the foreground signal.
 //
@@ -175,12 +178,16 @@ __device__ __forceinline__ float resid_exact(float d, float s0, float s1, float 
 
 
 __device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
+// first entry of the group of 32 cells that holds `cell` (entry e of the cell: [e * 32 + cell % 32])
+__device__ __forceinline__ long long mom_group(int cell) { return (long long)(cell >> 5) * NM * 32; }
+// cells of the moment scratch, rounded up to whole groups
+__host__ __device__ __forceinline__ long long mom_cells(long long ncell) { return (ncell + 31) & ~31LL; }
 
 // Floats of the per-thread evaluation rows at the start of the dynamic shared memory (moment path:
-// N A_1 and N A_2 per thread); the warp partials of the gradient follow them.
+// N A_1, N A_2, A_1, A_2, dA_1 and dA_2 per thread); the warp partials of the gradient follow them.
 template <int NT, int PATH>
 constexpr int fit_rows_floats() {
-  return PATH == CSX_PATH_MOMENT ? 30 * NT : 0;
+  return PATH == CSX_PATH_MOMENT ? 90 * NT : 0;
 }
 
 template <int NT, bool SEP, bool EXACT>
@@ -329,7 +336,7 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
           const int i = 4 * ba + ii, j = 4 * bb + jj;
-          if (i <= j && j < 18) c.mom[(long long)mom_index(i, j) * c.ncell + cell] = tot[ii * 4 + jj];
+          if (i <= j && j < 18) c.mom[mom_group(cell) + mom_index(i, j) * 32 + (cell & 31)] = tot[ii * 4 + jj];
         }
     }
     if (lane == 0) {
@@ -349,17 +356,23 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
 //   dL/dA  = -2 N [ D (Q Z + C^T N A) + P (C Z + R N A) ] M^-1       (Sec. 3.3.1, moment form)
 // D vanishes at beta_ref, so the rounding of the foreground-sized terms shrinks with |beta-beta_ref|.
 // Returns the sum of chi2_c; adds dL/dbeta into gacc (and the projected Gauss-Newton diagonal
-// into hacc). Per-thread rows in shared memory (stride NT): N A_1, N A_2 and R N A (75 floats).
+// into hacc). Per-thread rows in shared memory (stride NT), formed in the first pass over the
+// bands: N A_1, N A_2, A_1, A_2 and dA_1, dA_2 (90 floats).
+// Each warp takes groups of 32 cells (NT / 32 groups apart) and asks L2 for its next group while
+// it evaluates the current one (the first while the tables are formed): the moments of the CTAs'
+// problems together exceed L2, so without it every entry would wait on DRAM.
 template <int NT, bool WANT_H>
 __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
+  constexpr unsigned GROUP_BYTES = NM * 32 * sizeof(float);
+  if ((threadIdx.x & 31) == 0 && (threadIdx.x & ~31) < c.ncell)
+    prefetch_l2(c.mom + mom_group(threadIdx.x & ~31), GROUP_BYTES);
   partials_zero<NT>(c, WANT_H);
   fill_tables<NT>(a, c, c.x, c.tab);  // ends with a barrier
   const float* nb = a.ninv_band;
   float nsum = 0.f;
 #pragma unroll
   for (int f = 0; f < 15; ++f) nsum += nb[f];
-  float* row = c.smem + threadIdx.x;            // row[k * NT]: N A_1 (k = 0..14), N A_2 (15..29)
-  const int mst = c.ncell;
+  float* row = c.smem + threadIdx.x;  // row[k * NT]: N A_1 (k = 0..14), N A_2, A_1, A_2, dA_1, dA_2
   float acc = 0.f;  // per-thread sum over its few cells in FP32, FP64 across the block
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* gwv = c.gw + (long long)warp * c.P;
@@ -368,6 +381,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
   // warp's run scan combines the cells of one patch)
   for (int base = threadIdx.x & ~31; base < c.ncell; base += NT) {
     const int cell = base + lane;
+    if (lane == 0 && base + NT < c.ncell) prefetch_l2(c.mom + mom_group(base + NT), GROUP_BYTES);
     int kd = -1, kt = -1, ks = -1;
     float gbd = 0.f, gtd = 0.f, gbs = 0.f, h0 = 0.f, h1 = 0.f, h2 = 0.f;
     if (cell < c.ncell) do {
@@ -381,7 +395,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const float* pdr = c.tabr + kd * NB;
     const float* btr = c.tabr + (c.Kd + kt) * NB;
     const float* ssr = c.tabr + (c.Kd + 2 * c.KT + ks) * NB;
-    const float* ms = c.mom + cell;
+    const float* ms = c.mom + mom_group(cell) + lane;
     // M = A^T N A, Z = A_r^T N A and G = A^T N dA with dA = A - A_r (its first column is 0)
     float m01 = 0.f, m02 = 0.f, m11 = 0.f, m12 = 0.f, m22 = 0.f;
     float z10 = 0.f, z11 = 0.f, z12 = 0.f, z20 = 0.f, z21 = 0.f, z22 = 0.f;
@@ -394,6 +408,10 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       const float t1 = n * a1, t2 = n * a2;
       row[f * NT] = t1;
       row[(15 + f) * NT] = t2;
+      row[(30 + f) * NT] = a1;
+      row[(45 + f) * NT] = a2;
+      row[(60 + f) * NT] = a1 - r1;
+      row[(75 + f) * NT] = a2 - r2;
       m01 += t1;
       m02 += t2;
       m11 = fmaf(t1, a1, m11);
@@ -442,15 +460,15 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     float tdc = 0.f;
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
-      const float a1 = pd[f] * bt[f], a2 = ss[f];
-      const float e1 = a1 - pdr[f] * btr[f], e2 = a2 - ssr[f];
+      const float a1 = row[(30 + f) * NT], a2 = row[(45 + f) * NT];
+      const float e1 = row[(60 + f) * NT], e2 = row[(75 + f) * NT];
       const float na[3] = {nb[f], row[f * NT], row[(15 + f) * NT]};
       float D[3], C[3];
       D[0] = 0.f;
       D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
       D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * mst];
+      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * 32];
 #pragma unroll
       for (int k = 1; k < 3; ++k) {
         const float nd = nb[f] * D[k];
@@ -463,29 +481,45 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
         for (int l = 0; l < 3; ++l) CtA[k][l] = fmaf(C[k], na[l], CtA[k][l]);
     }
-    // B = R N A row by row, A^T N R N A, tr(N R), and the gradient part carried by B: with
-    // E = U + C Z + B - A Psi, the B term of E M^-1 in band i is sum_l B[i][l] M^-1[l][k]
-    float trNR = 0.f;
-    float AtRA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll 1
-    for (int i = 0; i < 15; ++i) {
-      float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    // B = R N A: every stored entry of R's upper triangle is read once and serves (i, j) and
+    // (j, i); N A_1, N A_2 held in registers. Then A^T N R N A, tr(N R), and the gradient part
+    // carried by B: with E = U + C Z + B - A Psi, the B term of E M^-1 in band i is
+    // sum_l B[i][l] M^-1[l][k]
+    float x1[15], x2[15], B[15][3];
 #pragma unroll
-      for (int j = 0; j < 15; ++j) {
-        const float s = (j >= i) ? ms[mom_index(i, j) * mst] : ms[mom_index(j, i) * mst];
-        b0 = fmaf(s, nb[j], b0);
-        b1 = fmaf(s, row[j * NT], b1);
-        b2 = fmaf(s, row[(15 + j) * NT], b2);
-        if (j == i) trNR = fmaf(nb[j], s, trNR);
+    for (int j = 0; j < 15; ++j) {
+      x1[j] = row[j * NT];
+      x2[j] = row[(15 + j) * NT];
+      B[j][0] = B[j][1] = B[j][2] = 0.f;
+    }
+    float trNR = 0.f;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+#pragma unroll
+      for (int j = i; j < 15; ++j) {
+        const float r = ms[mom_index(i, j) * 32];
+        B[i][0] = fmaf(r, nb[j], B[i][0]);
+        B[i][1] = fmaf(r, x1[j], B[i][1]);
+        B[i][2] = fmaf(r, x2[j], B[i][2]);
+        if (j == i) {
+          trNR = fmaf(nb[i], r, trNR);
+        } else {
+          B[j][0] = fmaf(r, nb[i], B[j][0]);
+          B[j][1] = fmaf(r, x1[i], B[j][1]);
+          B[j][2] = fmaf(r, x2[i], B[j][2]);
+        }
       }
-      const float na[3] = {nb[i], row[i * NT], row[(15 + i) * NT]};
-      const float bf[3] = {b0, b1, b2};
+    }
+    float AtRA[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      const float na[3] = {nb[i], x1[i], x2[i]};
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int l = 0; l < 3; ++l) AtRA[k][l] = fmaf(na[k], bf[l], AtRA[k][l]);
-      const float fb1 = b0 * v[0][1] + b1 * v[1][1] + b2 * v[2][1];
-      const float fb2 = b0 * v[0][2] + b1 * v[1][2] + b2 * v[2][2];
+        for (int l = 0; l < 3; ++l) AtRA[k][l] = fmaf(na[k], B[i][l], AtRA[k][l]);
+      const float fb1 = B[i][0] * v[0][1] + B[i][1] * v[1][1] + B[i][2] * v[2][1];
+      const float fb2 = B[i][0] * v[0][2] + B[i][1] * v[1][2] + B[i][2] * v[2][2];
       const float t1 = fb1 * na[1];
       gbd = fmaf(t1, a.bands.lnd[i], gbd);
       gtd = fmaf(t1, dt[i], gtd);
@@ -495,7 +529,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = ms[mom_index(15 + k, 15 + l) * mst];
+      for (int l = k; l < 3; ++l) Q[k][l] = Q[l][k] = ms[mom_index(15 + k, 15 + l) * 32];
     float chi = 2.f * tdc + trNR;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -520,14 +554,14 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     }
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
-      const float a1 = pd[f] * bt[f], a2 = ss[f];
-      const float e1 = a1 - pdr[f] * btr[f], e2 = a2 - ssr[f];
+      const float a1 = row[(30 + f) * NT], a2 = row[(45 + f) * NT];
+      const float e1 = row[(60 + f) * NT], e2 = row[(75 + f) * NT];
       float D[3], C[3];
       D[0] = 0.f;
       D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
       D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * mst];
+      for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * 32];
       float E[3];
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
@@ -551,7 +585,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       float n2[3] = {0.f, 0.f, 0.f};
 #pragma unroll 3
       for (int f = 0; f < 15; ++f) {
-        const float a1 = pd[f] * bt[f], a2 = ss[f];
+        const float a1 = row[(30 + f) * NT], a2 = row[(45 + f) * NT];
         const float da[3] = {a1 * a.bands.lnd[f], a1 * dt[f], a2 * a.bands.lns[f]};
 #pragma unroll
         for (int k = 0; k < 3; ++k) n2[k] = fmaf(nb[f] * da[k], da[k], n2[k]);
@@ -564,6 +598,13 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
     const int j1 = kt < 0 ? -1 : c.Kd + kt, j2 = ks < 0 ? -1 : c.Kd + c.KT + ks;
     warp_run_accum3(gwv, kd, gbd, j1, gtd, j2, gbs, sh.stage[warp]);
     if (WANT_H) warp_run_accum3(hwv, kd, h0, j1, h1, j2, h2, sh.stage[warp]);
+  }
+  // the optimiser's vectors and L-BFGS history (the slot's head, read next) were likely pushed
+  // out of L2 by the moments: ask for them back
+  if (threadIdx.x < 32) {
+    const unsigned long long bytes = (unsigned long long)(9 + 2 * a.history) * a.Pmax * sizeof(float);
+    for (unsigned long long off = (unsigned long long)threadIdx.x * 8192; off < bytes; off += 32 * 8192)
+      prefetch_l2(reinterpret_cast<const char*>(c.z) + off, (unsigned)min(8192ull, bytes - off));
   }
   partials_reduce<NT>(c, WANT_H);
   return block_sum<NT>((double)acc, sh.red);
@@ -750,7 +791,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       const float* Sk = c.S + (long long)k * a.Pmax;
       float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
       for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
-      const double dot = block_sum<NT>((double)dotf, sh.red);
+      const double dot = block_sum_f<NT>(dotf, sh.red);
       const double al = sh.rho[k] * dot;
       if (tid == 0) sh.alpha[k] = al;
       const float* Yk = c.Y + (long long)k * a.Pmax;
@@ -762,7 +803,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       const float* Yk = c.Y + (long long)k * a.Pmax;
       float dotf = 0.f;
       for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
-      const double dot = block_sum<NT>((double)dotf, sh.red);
+      const double dot = block_sum_f<NT>(dotf, sh.red);
       const double be = sh.rho[k] * dot;
       const float* Sk = c.S + (long long)k * a.Pmax;
       const float coef = (float)(sh.alpha[k] - be);
@@ -782,7 +823,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       gpf = fmaf(gi, pi, gpf);
       stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
     }
-    double gp = block_sum<NT>((double)gpf, sh.red);
+    double gp = block_sum_f<NT>(gpf, sh.red);
     stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
     if (!(gp < 0.0)) {
       // not a descent direction: restart from the projected steepest descent
@@ -801,7 +842,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
         gpf = fmaf(gi, pi, gpf);
         stepn = fmaxf(stepn, fabsf(pi) / c.hs[i] / a.xtol[t]);
       }
-      gp = block_sum<NT>((double)gpf, sh.red);
+      gp = block_sum_f<NT>(gpf, sh.red);
       stepn = block_max<NT>(stepn, reinterpret_cast<float*>(sh.red));
       if (!(gp < 0.0)) {
         status = CSX_FIT_CONVERGED;  // projected gradient vanishes
@@ -873,7 +914,7 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       }
       float dphif = 0.f;
       for (int i = tid; i < P; i += NT) dphif = fmaf(c.gt[i], c.p[i], dphif);
-      const double dphi = block_sum<NT>((double)dphif, sh.red);
+      const double dphi = block_sum_f<NT>(dphif, sh.red);
       if (!isfinite(ft) || !isfinite(dphi)) {
         a_hi = alpha;
         d_hi = 1.0;
@@ -950,8 +991,8 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       c.z[i] = c.zt[i];
       c.g[i] = c.gt[i];
     }
-    double sy = syf, yy = yyf;
-    block_sum2<NT>(sy, yy, sh.red);
+    double sy, yy;
+    block_sum2_f<NT>(syf, yyf, sh.red, sy, yy);
     sn = block_max<NT>(sn, reinterpret_cast<float*>(sh.red));
     last_step = sn;
     f = ft;
@@ -1313,8 +1354,8 @@ __device__ __forceinline__ void setup_ctx(const FitArgs& a, const ProbDesc& pd, 
   float* gwg = c.xr + Pm;  // warp partials in global memory: [8][Pmax] gradient, then GN diagonal
   c.gw = sm ? build_smem + fit_rows_floats<NT, PATH>() : gwg;
   c.hw = gwg + 8 * Pm;
-  c.mom = gwg + 16 * Pm;
-  c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * a.ncell_max);
+  c.mom = base + ((gwg + 16 * Pm - base + 31) & ~31LL);  // 128-byte aligned groups
+  c.trip = reinterpret_cast<int*>(c.mom + (long long)NM * mom_cells(a.ncell_max));
   c.smem = build_smem;
 }
 
@@ -1364,7 +1405,7 @@ int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path
   long long n = (long long)(9 + 2 * history) * Pmax + (long long)rows_max * NB;
   n += (long long)rows_max * NB + Pmax;  // reference tables and parameters (moment path)
   n += 16LL * Pmax;                      // warp partials (gradient, Gauss-Newton diagonal)
-  if (path == CSX_PATH_MOMENT) n += (long long)NM * ncell_max + 3LL * ncell_max;
+  if (path == CSX_PATH_MOMENT) n += 32 + (long long)NM * mom_cells(ncell_max) + 3LL * ncell_max;
   n = (n + 63) & ~63LL;
   *out = n;
   return CSX_OK;
@@ -1372,7 +1413,7 @@ int fit_slot_floats(int Pmax, int rows_max, int ncell_max, int history, int path
 
 template <int NT, int PATH>
 constexpr size_t fit_dyn_smem() {
-  // moment path: build staging (32 pixel rows per warp) or, during evaluations, 30 floats per
+  // moment path: build staging (32 pixel rows per warp) or, during evaluations, 90 floats per
   // thread followed by the warp partials; streaming path: the warp partials
   constexpr size_t build = (size_t)(NT / 32) * BUILD_SMEM_PER_WARP;
   constexpr size_t eval = (size_t)fit_rows_floats<NT, PATH>() + (size_t)(NT / 32) * SMEM_P;
