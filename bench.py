@@ -45,7 +45,8 @@ FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (F
 # kernel has been captured since its last change): the persistent fit per cell evaluation, the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
 TRAFFIC_FIT_PER_CELL_EVAL = None
-TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 129.5, "L": 129.5}
+TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": None, "L": None, "L_and_grad_unplanned": 129.5,
+                            "L_unplanned": 129.5}
 TRAFFIC_CAPTURE = {"fit": None,
                    "stream": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_spectral_tma, "
                              "full-sky nside 64, 100 realizations, per pixel evaluation"}
@@ -578,9 +579,24 @@ def streaming_rates(csx, hbm, ncall=20):
            "timing": "CUDA events around %d calls (tables kernel + memsets + streaming kernel)"
                      % ncall}
     from paper_2604_08463_b300 import autotune
-    for name, fn in (("L_and_grad", csx.spectral_grad), ("L", csx.spectral_like)):
+    # cell plan of the labels (label-only, built once; the beta-dependent per-cell scalars and band
+    # vectors are formed inside every timed call)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = csx.SpectralPlan(lab, K)
+    out["plan"] = {"cells": plan.ncell, "build_ms": (time.perf_counter() - t0) * 1e3,
+                   "timing": "host clock around csx_spectral_plan_create (synchronises)"}
+
+    def planned(grad):
+        return lambda model, sky, lab, K, beta: plan.grad(model, sky, beta, want_grad=grad)
+
+    legs = (("L_and_grad", planned(True), True, True), ("L", planned(False), False, True),
+            ("L_and_grad_unplanned", csx.spectral_grad, True, False),
+            ("L_unplanned", csx.spectral_like, False, False))
+    for name, fn, grad, use_plan in legs:
         # tile schedule chosen by timing every built schedule on this call shape (left in force)
-        sched, entry = autotune.tune_stream(csx, model, sky, lab, K, beta, grad=name == "L_and_grad")
+        sched, entry = autotune.tune_stream(csx, model, sky, lab, K, beta, grad=grad,
+                                            plan=plan if use_plan else None)
         for _ in range(3):
             fn(model, sky, lab, K, beta)
         torch.cuda.synchronize()
@@ -593,14 +609,20 @@ def streaming_rates(csx, hbm, ncall=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / ncall
         gbs = units * BYTES_PER_PIXEL_EVAL / (ms * 1e-3) / 1e9
+        tkey = ("L_and_grad" if grad else "L") + ("" if use_plan else "_unplanned")
         out[name] = {"ms_per_call": ms, "cluster_pixel_evals_per_s": units / (ms * 1e-3),
+                     "entry": "csx_spectral_grad_plan" if use_plan else
+                              ("csx_spectral_grad" if grad else "csx_spectral_like"),
                      "schedule": {"chosen": "%d/%d" % sched, "candidates_ms": entry["ms"],
                                   "unit": "pixels per tile / pipeline stages"},
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                   "frac": gbs / hbm,
-                                  "traffic": TRAFFIC_STREAM_PER_PIXEL[name] * units,
-                                  "traffic_source": TRAFFIC_CAPTURE["stream"]}}
+                                  "traffic": (TRAFFIC_STREAM_PER_PIXEL[tkey] * units
+                                              if TRAFFIC_STREAM_PER_PIXEL.get(tkey) else None),
+                                  "traffic_source": TRAFFIC_CAPTURE["stream"]
+                                  if TRAFFIC_STREAM_PER_PIXEL.get(tkey) else None}}
     csx.stream_schedule(0, 0)
+    plan.close()
     del d, sky
     torch.cuda.empty_cache()
     return out

@@ -226,6 +226,41 @@ int csx_spectral_grad_noalloc(const csx_model* m, const csx_sky* sky, const int3
                               float* grad, void* stream);
 
 /*
+ * Cell plan of a patch configuration for repeated streaming evaluations (Eqs. 3-4 over the patches
+ * of Sec. 2.2, gradient of Sec. 3.3.1): the label-only part of the streaming kernel, built once for
+ * labels that stay fixed while beta changes (an optimiser's loop). A cell is a set of pixels with
+ * equal (l_d, l_T, l_s); with homogeneous or separable noise every pixel of a cell shares the
+ * Gram-Schmidt factors of A^T N^-1 A and the band vectors of the likelihood and gradient, which
+ * csx_spectral_grad_plan forms once per (problem, cell) instead of once per run of equal labels in
+ * the pixel stream.
+ *   labels device int32 [3][npix];  K host int32[3]
+ *   plan   receives an opaque handle (owns device memory: npix + 4 ncell int32) on the current
+ *          device; release it with csx_spectral_plan_destroy.
+ * Synchronises `stream` (the cell count sizes the plan). Errors: CSX_EINVAL for a label outside
+ * [0, K_j), bad sizes or NULL pointers (nothing is allocated then); CSX_ECUDA.
+ */
+typedef struct csx_spectral_plan csx_spectral_plan;
+int csx_spectral_plan_create(int32_t npix, const int32_t* labels, const int32_t K[3], void* stream,
+                             csx_spectral_plan** plan);
+
+/* Frees the plan's device memory (after the device has finished any call that uses it). NULL is a
+ * no-op. */
+int csx_spectral_plan_destroy(csx_spectral_plan* plan);
+
+/* Cells of the plan (host int32). */
+int csx_spectral_plan_ncell(const csx_spectral_plan* plan, int32_t* ncell);
+
+/*
+ * L (and, if grad is not NULL, the adjoint gradient) of csx_spectral_like / csx_spectral_grad for
+ * the plan's labels and K: the same quantities up to FP32 rounding.
+ *   beta  device float [nprob][P];  L device double [nprob];  grad device float [nprob][P] or NULL
+ * Must run on the plan's device. Errors: CSX_EINVAL for per-pixel noise (no shared cell basis),
+ * a sky whose npix differs from the plan's, NULL or misaligned pointers.
+ */
+int csx_spectral_grad_plan(const csx_spectral_plan* plan, const csx_model* m, const csx_sky* sky,
+                           int32_t nprob, const float* beta, double* L, float* grad, void* stream);
+
+/*
  * L and dL/dbeta by the cell-moment evaluation that csx_fit_batch uses for homogeneous or separable
  * noise (Eq. 4 and Sec. 3.3.1 over the cells of equal (l_d, l_T, l_s), Sec. 2.2): for problem i
  * (realization i, nprob <= sky->nreal), the residual moments of each cell are formed about the

@@ -139,11 +139,12 @@ def tune_fit(csx, model, sky, labels, K, beta0, solver: str = "lbfgs", grad_mode
 
 
 # ------------------------------------------------------------------ streaming kernel schedule ----
-def stream_key(noise: str, npix: int, nprob: int, P: int, grad: bool) -> str:
-    """Cache key of a streaming call: noise model, gradient or not, and the powers of two nearest to
-    the pixel count, the number of problems and the parameter count."""
-    return "stream|%s|%s|n2^%d|q2^%d|P2^%d" % (noise, "grad" if grad else "like", _p2(npix),
-                                              _p2(nprob), _p2(P))
+def stream_key(noise: str, npix: int, nprob: int, P: int, grad: bool, plan: bool = False) -> str:
+    """Cache key of a streaming call: noise model, gradient or not, cell plan or not, and the
+    powers of two nearest to the pixel count, the number of problems and the parameter count."""
+    return "stream|%s|%s%s|n2^%d|q2^%d|P2^%d" % (noise, "grad" if grad else "like",
+                                                "|plan" if plan else "", _p2(npix), _p2(nprob),
+                                                _p2(P))
 
 
 def choose_schedule(key: str, cands, timer, cache=None, margin: float = MARGIN):
@@ -164,14 +165,19 @@ def choose_schedule(key: str, cands, timer, cache=None, margin: float = MARGIN):
     return (e["tile"], e["stages"]), e
 
 
-def tune_stream(csx, model, sky, labels, K, beta, grad: bool = True, ncall: int = 5, cache=None):
+def tune_stream(csx, model, sky, labels, K, beta, grad: bool = True, ncall: int = 5, cache=None,
+                plan=None):
     """Select the streaming kernel's tile schedule for calls shaped like this one (csx.spectral_grad
-    or csx.spectral_like of beta [nprob, P] on sky): each built schedule is timed with CUDA events
-    over `ncall` calls after one untimed call; the chosen schedule is left in force
-    (csx.stream_schedule). Returns ((tile, stages), table entry)."""
+    or csx.spectral_like of beta [nprob, P] on sky, or plan.grad of a csx.SpectralPlan): each built
+    schedule is timed with CUDA events over `ncall` calls after one untimed call; the chosen
+    schedule is left in force (csx.stream_schedule). Returns ((tile, stages), table entry)."""
     import torch
-    fn = csx.spectral_grad if grad else csx.spectral_like
-    key = stream_key(sky.noise, sky.npix, beta.shape[0], beta.shape[1], grad)
+    if plan is not None:
+        def fn(model, sky, labels, K, beta):
+            plan.grad(model, sky, beta, want_grad=grad)
+    else:
+        fn = csx.spectral_grad if grad else csx.spectral_like
+    key = stream_key(sky.noise, sky.npix, beta.shape[0], beta.shape[1], grad, plan is not None)
 
     def timer(tile, stages):
         csx.stream_schedule(tile, stages)

@@ -361,6 +361,147 @@ int csx_spectral_grad(const csx_model* m, const csx_sky* sky, const int32_t* lab
   return spectral_common(m, sky, labels, K, nprob, beta, L, grad, true, stream);
 }
 
+struct csx_spectral_plan {
+  int device;
+  int npix;
+  int K[3];
+  int ncell;
+  int* pcell;      // [npix] cell of each pixel
+  int4* cell_lab;  // [ncell] (l_d, l_T, l_s, 0)
+};
+
+int csx_spectral_plan_create(int32_t npix, const int32_t* labels, const int32_t K[3], void* stream,
+                             csx_spectral_plan** plan) {
+  if (!plan) return fail(CSX_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  if (npix < 0) return fail(CSX_EINVAL, "npix must be >= 0");
+  if (!K) return fail(CSX_EINVAL, "K is NULL");
+  int rc = check_K(K);
+  if (rc) return rc;
+  if (npix > 0 && !labels) return fail(CSX_EINVAL, "labels is NULL");
+  CSX_ALIGN(labels, 4);
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  CSX_CUDA(cudaGetDevice(&dev));
+  // temporaries of the cell sort: perm [npix], offsets [npix + 1], count, K
+  int* tmp = nullptr;
+  CSX_CUDA(cudaMalloc(&tmp, ((size_t)2 * npix + 8) * sizeof(int)));
+  int* perm = tmp;
+  int* off = tmp + npix;
+  int* nc = off + npix + 1;
+  int* Kd = nc + 1;
+  int ncell = 0;
+  auto cleanup = [&](int code) {
+    cudaFree(tmp);
+    return code;
+  };
+  if (cudaMemcpyAsync(Kd, K, 3 * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cleanup(fail(CSX_ECUDA, "copy of K"));
+  if (npix > 0 && (rc = launch_cells(npix, 1, labels, Kd, perm, off, nc, s))) return cleanup(rc);
+  if (npix > 0) {
+    if (cudaMemcpyAsync(&ncell, nc, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return cleanup(fail(CSX_ECUDA, "cell count"));
+  }
+  if (ncell < 0) return cleanup(fail(CSX_EINVAL, "a label is outside [0, K_j)"));
+  csx_spectral_plan* p = new csx_spectral_plan();
+  p->device = dev;
+  p->npix = npix;
+  for (int j = 0; j < 3; ++j) p->K[j] = K[j];
+  p->ncell = ncell;
+  void* mem = nullptr;
+  const size_t lab_off = (((size_t)npix * sizeof(int)) + 15) & ~size_t(15);
+  if (cudaMalloc(&mem, lab_off + (size_t)ncell * sizeof(int4) + 16) != cudaSuccess) {
+    delete p;
+    return cleanup(fail(CSX_ECUDA, "plan allocation"));
+  }
+  p->pcell = (int*)mem;
+  p->cell_lab = (int4*)((char*)mem + lab_off);
+  if ((rc = launch_plan_cells(npix, ncell, labels, perm, off, p->pcell, p->cell_lab, s)) ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(mem);
+    delete p;
+    return cleanup(rc ? rc : fail(CSX_ECUDA, "plan construction"));
+  }
+  *plan = p;
+  return cleanup(CSX_OK);
+}
+
+int csx_spectral_plan_destroy(csx_spectral_plan* plan) {
+  if (!plan) return CSX_OK;
+  int cur = 0;
+  CSX_CUDA(cudaGetDevice(&cur));
+  if (cur != plan->device) CSX_CUDA(cudaSetDevice(plan->device));
+  const cudaError_t e = cudaFree(plan->pcell);
+  if (cur != plan->device) cudaSetDevice(cur);
+  delete plan;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFree(plan)");
+  return CSX_OK;
+}
+
+int csx_spectral_plan_ncell(const csx_spectral_plan* plan, int32_t* ncell) {
+  if (!plan || !ncell) return fail(CSX_EINVAL, "NULL argument");
+  *ncell = plan->ncell;
+  return CSX_OK;
+}
+
+int csx_spectral_grad_plan(const csx_spectral_plan* plan, const csx_model* m, const csx_sky* sky,
+                           int32_t nprob, const float* beta, double* L, float* grad, void* stream) {
+  if (!plan) return fail(CSX_EINVAL, "plan is NULL");
+  int rc = check_model(m);
+  if (rc) return rc;
+  if ((rc = check_sky(sky, m->nfreq))) return rc;
+  if (sky->noise_kind == CSX_NOISE_PERPIXEL)
+    return fail(CSX_EINVAL, "the cell plan needs homogeneous or separable noise");
+  if (sky->npix != plan->npix) return fail(CSX_EINVAL, "sky->npix differs from the plan's npix");
+  if (nprob < 0 || nprob > sky->nreal) return fail(CSX_EINVAL, "nprob must be in [0, sky->nreal]");
+  if (nprob == 0) return CSX_OK;
+  if (!beta || !L) return fail(CSX_EINVAL, "beta and L must not be NULL");
+  CSX_ALIGN(beta, 4);
+  CSX_ALIGN(L, 8);
+  CSX_ALIGN(grad, 4);
+  int dev = 0;
+  CSX_CUDA(cudaGetDevice(&dev));
+  if (dev != plan->device) return fail(CSX_EINVAL, "the plan belongs to another device");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int* K = plan->K;
+  const int P = K[0] + K[1] + K[2];
+  const int rows = K[0] + 2 * K[1] + K[2];
+  const Bands b = make_bands(*m);
+  float* tables = (float*)scratch(SCR_TABLES, (size_t)nprob * rows * NB * sizeof(float), &rc);
+  if (rc) return rc;
+  float* ctab = (float*)scratch(SCR_CELLTAB, (size_t)nprob * plan->ncell * CELL_TAB * sizeof(float), &rc);
+  if (rc) return rc;
+  if ((rc = launch_tables(b, nprob, K[0], K[1], K[2], beta, tables, s))) return rc;
+  CSX_CUDA(cudaMemsetAsync(L, 0, (size_t)nprob * sizeof(double), s));
+  if (grad) CSX_CUDA(cudaMemsetAsync(grad, 0, (size_t)nprob * P * sizeof(float), s));
+  if (sky->npix == 0) return CSX_OK;
+  SpecArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.bands = b;
+  a.npix = sky->npix;
+  a.nprob = nprob;
+  a.Kd = K[0];
+  a.KT = K[1];
+  a.Ks = K[2];
+  a.P = P;
+  a.rows = rows;
+  a.noise_kind = sky->noise_kind;
+  a.d = sky->d;
+  a.w = sky->w;
+  copy_band_weights(sky, m->nfreq, a.ninv_band);
+  a.beta = beta;
+  a.tables = tables;
+  a.L = L;
+  a.grad = grad;
+  a.pcell = plan->pcell;
+  a.cell_lab = plan->cell_lab;
+  a.ncell = plan->ncell;
+  if ((rc = launch_cell_tables(a, grad != nullptr, ctab, s))) return rc;
+  a.ctab = ctab;
+  return launch_spectral(a, grad != nullptr, s);
+}
+
 int csx_spectral_grad_f64(const csx_model* m, const csx_sky* sky, const int32_t* labels,
                           const int32_t K[3], int32_t nprob, const double* beta, double* L,
                           double* grad, void* stream) {

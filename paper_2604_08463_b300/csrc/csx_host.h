@@ -31,6 +31,7 @@ enum ScratchId {
   SCR_RECON_DESC,
   SCR_KMEANS,       // K-means: per-labeling best dot products, cluster counts and offsets
   SCR_SHT,          // pseudo-C_ell: ring coefficients of a chunk of maps
+  SCR_CELLTAB,      // per-(problem, cell) scalars and band vectors of csx_spectral_grad_plan
   SCR_COUNT
 };
 void* scratch(ScratchId id, size_t bytes, int* err);
@@ -65,7 +66,18 @@ struct SpecArgs {
   const float* tables;   // [nprob][rows][16]
   double* L;
   float* grad;
+  // cell plan (csx_spectral_plan; separable / homogeneous noise): each pixel's cell, the cells'
+  // labels, and per problem and cell the Gram-Schmidt scalars and band vectors [nprob][ncell][96]
+  const int* pcell;
+  const int4* cell_lab;
+  const float* ctab;
+  int ncell;
 };
+// Floats of one (problem, cell) entry of the cell tables: 16 scalars (run_scalars) + 5 band vectors.
+constexpr int CELL_TAB = 96;
+int launch_cell_tables(const SpecArgs& a, bool grad, float* ctab, cudaStream_t s);
+int launch_plan_cells(int npix, int ncell, const int* labels, const int* perm, const int* cell_off,
+                      int* pcell, int4* cell_lab, cudaStream_t s);
 int launch_tables(const Bands& b, int nprob, int Kd, int KT, int Ks, const float* beta,
                   float* tables, cudaStream_t s);
 

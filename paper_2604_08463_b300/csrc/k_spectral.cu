@@ -88,6 +88,69 @@ int launch_mixing(const Bands& b, int n, const float* beta, float* A, float* dA,
 }
 
 // ---------------------------------------------------------------------------------------------
+// Cell plan. Every pixel of a cell (equal (l_d, l_T, l_s)) shares its Gram-Schmidt scalars and band
+// vectors (see run_scalars), so they are formed once per (problem, cell) by one thread each, before
+// the streaming kernel, instead of once per run of equal labels inside it.
+template <bool GRAD>
+__global__ void k_cell_tables(const SpecArgs a, float* __restrict__ ctab) {
+  float n0 = 0.f;
+#pragma unroll
+  for (int f = 0; f < NB; ++f) n0 += a.ninv_band[f];
+  const long long total = (long long)a.nprob * a.ncell;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / a.ncell), c = (int)(i % a.ncell);
+    const int4 t = a.cell_lab[c];
+    const float* tab = a.tables + (long long)q * a.rows * NB;
+    float* out = ctab + i * CELL_TAB;
+    run_scalars<GRAD>(tab + (long long)t.x * NB, tab + (long long)(a.Kd + t.y) * NB,
+                      tab + (long long)(a.Kd + a.KT + t.y) * NB,
+                      tab + (long long)(a.Kd + 2 * a.KT + t.z) * NB, a.ninv_band, a.bands, n0, out,
+                      out + 16);
+  }
+}
+
+int launch_cell_tables(const SpecArgs& a, bool grad, float* ctab, cudaStream_t s) {
+  const long long total = (long long)a.nprob * a.ncell;
+  if (total == 0) return CSX_OK;
+  const long long blocks = (total + 127) / 128;
+  const int g = (int)(blocks < 148 * 16 ? blocks : 148 * 16);
+  if (grad) k_cell_tables<true><<<g, 128, 0, s>>>(a, ctab);
+  else k_cell_tables<false><<<g, 128, 0, s>>>(a, ctab);
+  CSX_CUDA(cudaGetLastError());
+  return CSX_OK;
+}
+
+// Each pixel's cell and each cell's labels from the sorted cell structure of launch_cells: sorted
+// position i belongs to the cell c with cell_off[c] <= i < cell_off[c + 1] (binary search).
+__global__ void k_plan_cells(int npix, int ncell, const int* __restrict__ labels,
+                             const int* __restrict__ perm, const int* __restrict__ cell_off,
+                             int* __restrict__ pcell, int4* __restrict__ cell_lab) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = ncell - 1;  // largest c with cell_off[c] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (cell_off[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const int px = perm[i];
+    pcell[px] = lo;
+    if (cell_off[lo] == i)
+      cell_lab[lo] = make_int4(labels[px], labels[npix + px], labels[2 * npix + px], 0);
+  }
+}
+
+int launch_plan_cells(int npix, int ncell, const int* labels, const int* perm, const int* cell_off,
+                      int* pcell, int4* cell_lab, cudaStream_t s) {
+  if (npix == 0 || ncell <= 0) return CSX_OK;
+  const int blocks = (npix + 255) / 256;
+  k_plan_cells<<<blocks < 148 * 8 ? blocks : 148 * 8, 256, 0, s>>>(npix, ncell, labels, perm,
+                                                                   cell_off, pcell, cell_lab);
+  CSX_CUDA(cudaGetLastError());
+  return CSX_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Streaming likelihood (+ gradient) of Eqs. 3-4 and Sec. 3.3.1, TMA-staged. Grid (pixel blocks,
 // problems); a CTA takes a contiguous range of tiles of TS_NT consecutive pixels of its problem
 // (CSX_TS_CONTIG; else tiles strided by the grid). One thread keeps up to TS_S tiles of d (and of N^-1 for per-pixel
@@ -135,11 +198,12 @@ constexpr bool TS_WARPRUNS = CSX_TS_WARPRUNS != 0;
 constexpr bool TS_CONTIG = CSX_TS_CONTIG != 0;
 constexpr bool TS_RUNCACHE = CSX_TS_RUNCACHE != 0;
 
-template <int NOISE, int TS_NT, int TS_S>
+template <int NOISE, int TS_NT, int TS_S, bool CELLS = false>
 struct TsShape {
-  static constexpr bool RUNS = NOISE != CSX_NOISE_PERPIXEL;
+  static constexpr bool PIXNOISE = NOISE == CSX_NOISE_PERPIXEL;         // N^-1 staged per pixel
+  static constexpr bool RUNS = !PIXNOISE && !CELLS;                      // in-kernel run table
   static constexpr int DB = TS_NT * 128;                                 // d: [TS_NT][2][16] floats
-  static constexpr int NBY = RUNS ? 0 : TS_NT * 64;                      // N^-1: [TS_NT][16] floats
+  static constexpr int NBY = PIXNOISE ? TS_NT * 64 : 0;                  // N^-1: [TS_NT][16] floats
   static constexpr int SB = DB + NBY;                                    // bytes per stage
   static constexpr int RB = RUNS ? TS_NT * (16 * 4 + 16) + TS_RUNVEC * 80 * 4 : 0;  // run table
   static constexpr size_t smem(int P, bool smem_grad) {
@@ -147,13 +211,13 @@ struct TsShape {
   }
 };
 
-template <int NOISE, bool GRAD, bool SMEM_GRAD, int TS_NT, int TS_S>
+template <int NOISE, bool GRAD, bool SMEM_GRAD, int TS_NT, int TS_S, bool CELLS>
 __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     k_spectral_tma(const __grid_constant__ CUtensorMap md, const __grid_constant__ CUtensorMap mn,
                    const SpecArgs a) {
   constexpr int TS_NW = TS_NT / 32;
   constexpr int TS_RUNVEC_W = TS_RUNVEC / TS_NW;  // run vectors per warp
-  using Sh = TsShape<NOISE, TS_NT, TS_S>;
+  using Sh = TsShape<NOISE, TS_NT, TS_S, CELLS>;
   extern __shared__ __align__(16) unsigned char ts_smem[];
   __shared__ __align__(8) uint64_t full[TS_S];
   __shared__ double sred[TS_NW];
@@ -195,14 +259,18 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
   const int* ld = a.labels;
   const int* lt = a.labels + a.npix;
   const int* ls = a.labels + 2 * a.npix;
-  int nkd = 0, nkt = 0, nks = 0;
+  int nkd = 0, nkt = 0, nks = 0, ncl = 0;
   float nw = 1.f;
   auto fetch = [&](int j) {
     const int p = (t0 + j * tstep) * TS_NT + tid;
     if (j < my && p < a.npix) {
-      nkd = __ldg(ld + p);
-      nkt = __ldg(lt + p);
-      nks = __ldg(ls + p);
+      if (CELLS) {
+        ncl = __ldg(a.pcell + p);
+      } else {
+        nkd = __ldg(ld + p);
+        nkt = __ldg(lt + p);
+        nks = __ldg(ls + p);
+      }
       if (NOISE == CSX_NOISE_SEPARABLE) nw = __ldg(a.w + p);
     }
   };
@@ -214,7 +282,7 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
   bool bad = false;
   int j = 0;
   bool timed_out = false;
-  constexpr bool WR = Sh::RUNS && TS_WARPRUNS;
+  constexpr bool WR = Sh::RUNS && TS_WARPRUNS && !CELLS;
   int wnent = 0;  // entries of this warp's run cache
   for (; j < my; ++j) {
     const int s = j % TS_S;
@@ -286,12 +354,30 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
       }
     }
     int kd = nkd, kt = nkt, ks = nks;
+    const int cl = ncl;
     const float wp = nw;
     fetch(j + 1);
+    if (CELLS) {
+      // the next tile's cells: the first lane of each run of equal cells asks L1 for the cell's
+      // table entry (3 lines) and labels, a tile before they are read
+      const int pc = __shfl_up_sync(0xffffffffu, ncl, 1);
+      if ((lane == 0 || ncl != pc) && j + 1 < my) {
+        const char* e = reinterpret_cast<const char*>(a.ctab + ((long long)q * a.ncell + ncl) * CELL_TAB);
+        prefetch_l1(e);
+        prefetch_l1(e + 128);
+        prefetch_l1(e + 256);
+        if (GRAD) prefetch_l1(a.cell_lab + ncl);
+      }
+    }
     const int p = (t0 + j * tstep) * TS_NT + tid;
     bool valid = p < a.npix;
-    if (valid && ((unsigned)kd >= (unsigned)a.Kd || (unsigned)kt >= (unsigned)a.KT ||
-                  (unsigned)ks >= (unsigned)a.Ks)) {
+    if (CELLS) {
+      if (valid && (unsigned)cl >= (unsigned)a.ncell) {
+        bad = true;
+        valid = false;
+      }
+    } else if (valid && ((unsigned)kd >= (unsigned)a.Kd || (unsigned)kt >= (unsigned)a.KT ||
+                         (unsigned)ks >= (unsigned)a.Ks)) {
       bad = true;
       valid = false;
     }
@@ -299,7 +385,7 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     // pixel or where a label changes
     bool head = false;
     unsigned hb = 0u;
-    if (Sh::RUNS && !WR) {
+    if (Sh::RUNS && !WR && !CELLS) {
       const int pkd = __shfl_up_sync(0xffffffffu, kd, 1), pkt = __shfl_up_sync(0xffffffffu, kt, 1),
                 pks = __shfl_up_sync(0xffffffffu, ks, 1);
       const bool pv = __shfl_up_sync(0xffffffffu, valid, 1);
@@ -313,7 +399,22 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     }
     if (tid == 0 && j + TS_S < my) issue(j + TS_S);
     float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (WR) {
+    if (CELLS) {
+      // the cell's scalars and band vectors were formed for this problem before the launch
+      if (valid) {
+        const float* ct = a.ctab + ((long long)q * a.ncell + cl) * CELL_TAB;
+        float sc[NSC];
+        load_scalars(ct, sc);
+        const float wpx = NOISE == CSX_NOISE_SEPARABLE ? wp : 1.f;
+        acc += cell_pixel_vec<GRAD>(dq, du, a.ninv_band, ct + 16, sc, wpx, g0, g1, g2);
+        if (GRAD) {
+          const int4 t = __ldg(a.cell_lab + cl);
+          kd = t.x;
+          kt = t.y;
+          ks = t.z;
+        }
+      }
+    } else if (WR) {
       if (valid) {  // the block barrier above published the warp's run table
         float sc[NSC];
         load_scalars(s_sc + 16 * (warp * 32 + wslot), sc);
@@ -401,26 +502,26 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
   }
 }
 
-template <int NOISE, bool GRAD, bool SMEM_GRAD, int NT, int S>
+template <int NOISE, bool GRAD, bool SMEM_GRAD, int NT, int S, bool CELLS>
 static int launch_tma_one(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, dim3 grid,
                           cudaStream_t s) {
-  using Sh = TsShape<NOISE, NT, S>;
+  using Sh = TsShape<NOISE, NT, S, CELLS>;
   const size_t smem = Sh::smem(a.P, GRAD && SMEM_GRAD);
   // the attribute covers the ring plus a P-vector of up to 16384 floats
-  CSX_CUDA(cudaFuncSetAttribute(k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S>,
+  CSX_CUDA(cudaFuncSetAttribute(k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S, CELLS>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Sh::smem(16384, true)));
-  k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S><<<grid, NT, smem, s>>>(md, mn, a);
+  k_spectral_tma<NOISE, GRAD, SMEM_GRAD, NT, S, CELLS><<<grid, NT, smem, s>>>(md, mn, a);
   CSX_CUDA(cudaGetLastError());
   return CSX_OK;
 }
 
-template <int NOISE, int NT, int S>
+template <int NOISE, int NT, int S, bool CELLS>
 static int launch_tma(const CUtensorMap& md, const CUtensorMap& mn, const SpecArgs& a, bool grad,
                       dim3 grid, cudaStream_t s) {
-  if (!grad) return launch_tma_one<NOISE, false, false, NT, S>(md, mn, a, grid, s);
-  if (a.P <= 16384) return launch_tma_one<NOISE, true, true, NT, S>(md, mn, a, grid, s);
-  return launch_tma_one<NOISE, true, false, NT, S>(md, mn, a, grid, s);
+  if (!grad) return launch_tma_one<NOISE, false, false, NT, S, CELLS>(md, mn, a, grid, s);
+  if (a.P <= 16384) return launch_tma_one<NOISE, true, true, NT, S, CELLS>(md, mn, a, grid, s);
+  return launch_tma_one<NOISE, true, false, NT, S, CELLS>(md, mn, a, grid, s);
 }
 
 // Tensor maps of one launch: d as [problems][npix][32 floats] (box 32 x 256 x 1, 128-byte
@@ -490,10 +591,15 @@ static int launch_sched(const SpecArgs& b, bool grad, cudaStream_t s) {
   CUtensorMap md, mn;
   if (!make_maps(b, &md, &mn, NT)) return fail(CSX_ECUDA, "tensor-map encoding failed (cuTensorMapEncodeTiled)");
   const dim3 grid(tma_grid_x(b.npix, b.nprob, NT), b.nprob);
+  if (b.pcell) {  // cell plan: separable or homogeneous noise only (checked by the entry point)
+    if (b.noise_kind == CSX_NOISE_HOMOGENEOUS)
+      return launch_tma<CSX_NOISE_HOMOGENEOUS, NT, S, true>(md, mn, b, grad, grid, s);
+    return launch_tma<CSX_NOISE_SEPARABLE, NT, S, true>(md, mn, b, grad, grid, s);
+  }
   switch (b.noise_kind) {
-    case CSX_NOISE_HOMOGENEOUS: return launch_tma<CSX_NOISE_HOMOGENEOUS, NT, S>(md, mn, b, grad, grid, s);
-    case CSX_NOISE_SEPARABLE: return launch_tma<CSX_NOISE_SEPARABLE, NT, S>(md, mn, b, grad, grid, s);
-    default: return launch_tma<CSX_NOISE_PERPIXEL, NT, S>(md, mn, b, grad, grid, s);
+    case CSX_NOISE_HOMOGENEOUS: return launch_tma<CSX_NOISE_HOMOGENEOUS, NT, S, false>(md, mn, b, grad, grid, s);
+    case CSX_NOISE_SEPARABLE: return launch_tma<CSX_NOISE_SEPARABLE, NT, S, false>(md, mn, b, grad, grid, s);
+    default: return launch_tma<CSX_NOISE_PERPIXEL, NT, S, false>(md, mn, b, grad, grid, s);
   }
 }
 
@@ -510,6 +616,7 @@ int launch_spectral(const SpecArgs& a, bool grad, cudaStream_t s) {
     b.beta = a.beta + (long long)q0 * a.P;
     b.L = a.L + q0;
     b.grad = a.grad ? a.grad + (long long)q0 * a.P : nullptr;
+    b.ctab = a.ctab ? a.ctab + (long long)q0 * a.ncell * CELL_TAB : nullptr;
     int rc;
     switch (sched) {
       case 1: rc = launch_sched<64, 2>(b, grad, s); break;

@@ -25,7 +25,8 @@ M_SYS_SQ, M_STAT, M_CMB_Q, M_CMB_Q2, M_CMB_U, M_CMB_U2, M_NPIX = range(7)
 EXPORTS = ["csx_version", "csx_last_error", "csx_release", "csx_device_status",
            "csx_stream_schedule", "csx_fit_defaults", "csx_mixing",
            "csx_spectral_like", "csx_spectral_grad", "csx_spectral_grad_f64",
-           "csx_spectral_grad_noalloc",
+           "csx_spectral_grad_noalloc", "csx_spectral_plan_create", "csx_spectral_plan_destroy",
+           "csx_spectral_plan_ncell", "csx_spectral_grad_plan",
            "csx_cell_like_grad", "csx_build_cells", "csx_fit_batch", "csx_reconstruct",
            "csx_select", "csx_kmeans", "csx_sht_plan_create", "csx_sht_plan_destroy",
            "csx_pseudo_cl", "csx_residual_cl"]
@@ -79,6 +80,10 @@ def lib():
                                             vp, vp]
         L.csx_spectral_grad_noalloc.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp,
                                                 vp, vp, vp]
+        L.csx_spectral_plan_create.argtypes = [i32, vp, pi32, vp, POINTER(c_void_p)]
+        L.csx_spectral_plan_destroy.argtypes = [vp]
+        L.csx_spectral_plan_ncell.argtypes = [vp, pi32]
+        L.csx_spectral_grad_plan.argtypes = [vp, POINTER(CModel), POINTER(CSky), i32, vp, vp, vp, vp]
         L.csx_cell_like_grad.argtypes = [POINTER(CModel), POINTER(CSky), vp, pi32, i32, vp, vp,
                                          vp, vp, vp]
         L.csx_build_cells.argtypes = [i32, i32, vp, pi32, vp, vp, vp, vp]
@@ -235,6 +240,43 @@ def spectral_grad(model: Model, sky: Sky, labels, K, beta):
     _check(lib().csx_spectral_grad(ctypes.byref(model.c), ctypes.byref(sky.c), _ptr(labels), Kp,
                                    beta.shape[0], _ptr(beta), _ptr(L), _ptr(g), _stream()))
     return L, g
+
+
+class SpectralPlan:
+    """Cell plan of one patch configuration (labels [3, npix] int32 on the device, K) for repeated
+    streaming evaluations at changing beta (csx_spectral_plan_create; freed with the object)."""
+
+    def __init__(self, labels: torch.Tensor, K):
+        K, Kp = _host_i32(K)
+        self.K = K
+        self.npix = int(labels.shape[-1])
+        self._labels = labels  # kept alive while the plan is built
+        h = c_void_p()
+        _check(lib().csx_spectral_plan_create(self.npix, _ptr(labels), Kp, _stream(), ctypes.byref(h)))
+        self._h = h
+        n = c_int32()
+        _check(lib().csx_spectral_plan_ncell(self._h, ctypes.byref(n)))
+        self.ncell = int(n.value)
+
+    def grad(self, model: "Model", sky: "Sky", beta, want_grad=True):
+        """(L [nprob] float64, grad [nprob, P] float32 or None) of csx_spectral_grad_plan."""
+        beta = beta.to(torch.float32).contiguous()
+        L = torch.empty(beta.shape[0], device=beta.device, dtype=torch.float64)
+        g = torch.empty_like(beta) if want_grad else None
+        _check(lib().csx_spectral_grad_plan(self._h, ctypes.byref(model.c), ctypes.byref(sky.c),
+                                            beta.shape[0], _ptr(beta), _ptr(L), _ptr(g), _stream()))
+        return L, g
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(lib().csx_spectral_plan_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def spectral_grad_f64(model: Model, sky: Sky, labels, K, beta, want_grad=True):

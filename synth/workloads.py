@@ -114,6 +114,22 @@ def scan(nside: int = 64, nconf: int = 1000, kmax: int = 500, nreal: int = 10,
     return Workload(name, sk, Kc, labels, nreal, "separable", meta={"K_requested": kreq})
 
 
+def scan_subset(configs, nside: int = 64, nconf: int = 4000, kmax: int = 1000, nreal: int = 1,
+                b_cut_deg: float = 20.0, seed: int = 4) -> Workload:
+    """The configurations `configs` (indices into the K sample of scan(nside, nconf, kmax, seed))
+    of that scan, alone: same sky, same K draws and the same K-means labelings, without forming the
+    other configurations' labels (the full-pipeline scan has 4000 configurations)."""
+    pix = healpix.galactic_cut(nside, b_cut_deg)
+    sk = skymod.make_sky(nside, pix=pix, truth="smooth", hitcount=True)
+    vec = healpix.unit_vectors(nside)[pix]
+    kreq = sample_patch_counts(nconf, kmax, seed)[np.asarray(configs, dtype=np.int64)]
+    Kc, labels = _labels_for(vec, kreq, key="cut%d_%g" % (nside, b_cut_deg))
+    name = "scan_nside%d_b%g_C%d_K%d_subset%s" % (nside, b_cut_deg, nconf, kmax,
+                                                 "-".join(str(int(c)) for c in configs))
+    return Workload(name, sk, Kc, labels, nreal, "separable",
+                    meta={"K_requested": kreq, "configs": list(configs)})
+
+
 def gradcheck(nside: int = 128, K=(256, 256, 256), npoints: int = 64) -> Workload:
     """Full sky at nside 128, smooth truth, hit-count noise, K = 256 per parameter; one realization."""
     w = fullsky(nside, K, nreal=1)

@@ -63,10 +63,18 @@ def _multires16():
     return workloads.Workload("multires16", sk, K[None], lab[None], 2, "separable")
 
 
+def _pipeline64():
+    """The two largest-P configurations of the full-pipeline scan (nside 64, |b| > 20 deg, 4000
+    configurations, K log-uniform up to 1000): requested K (872, 874, 843) and (963, 899, 139)."""
+    from synth import workloads
+    return workloads.scan_subset([937, 1739], nside=64, nconf=4000, kmax=1000, nreal=1)
+
+
 CASES = {
     "scan64": (_scan64, _scan64_picks),
     "scan16_k1000": (_scan16, _scan16_picks),
     "multires16": (_multires16, lambda wl: [0, 1]),
+    "pipeline64": (_pipeline64, lambda wl: [0, 1]),
 }
 
 

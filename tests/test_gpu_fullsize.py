@@ -163,6 +163,28 @@ def test_large_k_scan_nside16_sampled_problems(csx):
     _sampled_fit_check(csx, case, res, picks, max_alternative=0.01, refs=refs)
 
 
+def test_pipeline_largest_p_sampled_problems(csx):
+    """The two largest-P configurations of the full-pipeline scan (nside 64, |b| > 20 deg, K per
+    parameter log-uniform up to 1000; P = 2589 and 2001, realization 0) fitted in one launch,
+    against stored oracle fits (tests/golden/make_fit_refs.py, case pipeline64)."""
+    import os
+    from tests.golden import make_fit_refs as mk
+    if not os.path.exists(os.path.join(os.path.dirname(mk.__file__), "fit_refs_pipeline64.npz")):
+        pytest.skip("stored oracle fits of the pipeline case not written")
+    wl = workloads.scan_subset([937, 1739], nside=64, nconf=4000, kmax=1000, nreal=1)
+    case = Case(wl, "separable")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(pack(wl, [wl.beta0(c) for c in range(wl.nconf) for _ in range(wl.nreal)]),
+                         device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0)
+    torch.cuda.synchronize()
+    picks, refs = stored_refs("pipeline64", case)
+    print("P", wl.P.tolist())
+    # patches of ~12 pixels (P ~ 2600 over 32512 pixels): up to 1% of the parameters may sit at
+    # another optimum as good in FP64 (within 1e-6 chi2)
+    _sampled_fit_check(csx, case, res, picks, max_alternative=0.01, refs=refs)
+
+
 def test_cell_moment_evaluation_nside64_scan(csx):
     """The fit's cell-moment evaluation of L and dL/dbeta at fixed points, on configurations of the
     bench's nside-64 scan (small, median and large P), against the oracle's pixel-by-pixel

@@ -110,6 +110,73 @@ def test_spectral_kmeans_patches(noise):
         assert_grad_close(g[r], gr, Sr)
 
 
+@pytest.mark.parametrize("noise", ["homogeneous", "separable"])
+@pytest.mark.parametrize("nside,K", [(8, (5, 3, 4)), (16, (12, 3, 6)), (16, (40, 7, 12))])
+def test_spectral_plan_matches_oracle(noise, nside, K):
+    """The cell-plan evaluation (scalars and band vectors formed per (problem, cell) before the
+    streaming kernel): L and the adjoint gradient against the oracle, L alone as well, at K-means
+    patches (warps holding one to several runs of a cell) and random beta."""
+    csx = _csx()
+    case = Case(workloads.fullsky(nside, K, nreal=3), noise)
+    model, sky, labels = case.gpu()
+    lab = case.wl.labels[0]
+    plan = csx.SpectralPlan(labels[0], K)
+    assert plan.ncell == len(set(zip(*lab)))
+    beta = workloads.random_points(np.array(K), 3, seed=nside + 7).astype(np.float32)
+    bt = torch.tensor(beta, device="cuda")
+    L2, g = plan.grad(model, sky, bt)
+    L1, none = plan.grad(model, sky, bt, want_grad=False)
+    torch.cuda.synchronize()
+    assert none is None
+    L1, L2, g = L1.cpu().numpy(), L2.cpu().numpy(), g.cpu().numpy()
+    for r in range(3):
+        Lr, gr, Sr = grad_ref(case, r, lab, K, beta[r].astype(np.float64))
+        assert abs(L1[r] - Lr) <= 1e-5 * abs(Lr), (L1[r], Lr)
+        assert abs(L2[r] - Lr) <= 1e-5 * abs(Lr), (L2[r], Lr)
+        assert_grad_close(g[r], gr, Sr)
+    plan.close()
+
+
+def test_spectral_plan_ragged_tail_one_pixel_cells_and_refusals():
+    """300 pixels (a ragged last tile), every pixel its own beta_d patch (one-pixel cells); labels
+    outside [0, K_j) refuse the plan on the host; per-pixel noise and a sky of another size refuse
+    the evaluation."""
+    csx = _csx()
+    case = small_case(nside=8, K=(768, 2, 3), nreal=1, noise="separable")
+    keep = 300
+    lab = np.ascontiguousarray(case.wl.labels[0][:, :keep])
+    lab[0] = np.arange(keep)
+    K = (keep, 2, 3)
+    d = torch.tensor(case.d32[:, :keep], device="cuda")
+    sky = csx.Sky(d, noise="separable", ninv_band=case.nb32,
+                  w=torch.tensor(case.w32[:keep], device="cuda"))
+    model = csx.Model(case.nu)
+    beta = workloads.random_points(np.array(K), 1, seed=5).astype(np.float32)
+    plan = csx.SpectralPlan(torch.tensor(lab, device="cuda"), K)
+    assert plan.ncell == keep
+    L, g = plan.grad(model, sky, torch.tensor(beta, device="cuda"))
+    torch.cuda.synchronize()
+    Lr, gr, Sr = grad_ref(case, 0, lab, K, beta[0].astype(np.float64),
+                          d64=case.d64(0)[:keep], ninv=case.ninv64[:keep])
+    assert abs(L.item() - Lr) <= 1e-5 * abs(Lr)
+    Sd = lk.gradient_term_scale(case.nu, case.d64(0)[:keep], case.ninv64[:keep], lab, K,
+                                beta[0].astype(np.float64), data_scale=True)
+    assert_grad_close(g.cpu().numpy()[0], gr, Sr + 16 * 2.0 ** -24 / 1e-5 * Sd)
+    assert_grad_close(g.cpu().numpy()[0][keep:], gr[keep:], Sr[keep:])
+    bad = lab.copy()
+    bad[1, 17] = 2  # K_T = 2
+    with pytest.raises(csx.CsxError, match="outside"):
+        csx.SpectralPlan(torch.tensor(bad, device="cuda"), K)
+    other = small_case(nside=8, K=(5, 3, 4), nreal=1, noise="perpixel")
+    m2, sky_pp, _ = other.gpu()
+    with pytest.raises(csx.CsxError, match="per-pixel|homogeneous or separable"):
+        plan.grad(m2, sky_pp, torch.zeros((1, sum(K)), device="cuda"))
+    sep = small_case(nside=8, K=(5, 3, 4), nreal=1, noise="separable")
+    m3, sky_768, _ = sep.gpu()
+    with pytest.raises(csx.CsxError, match="npix"):
+        plan.grad(m3, sky_768, torch.zeros((1, sum(K)), device="cuda"))
+
+
 def test_spectral_misaligned_data_is_refused():
     """Data not 16-byte aligned cannot be read as 16-byte pixel vectors nor staged by tensor copies:
     the call is refused on the host with CSX_EINVAL, nothing is launched, and the same data from an
