@@ -357,18 +357,6 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     const int cl = ncl;
     const float wp = nw;
     fetch(j + 1);
-    if (CELLS) {
-      // the next tile's cells: the first lane of each run of equal cells asks L1 for the cell's
-      // table entry (3 lines) and labels, a tile before they are read
-      const int pc = __shfl_up_sync(0xffffffffu, ncl, 1);
-      if ((lane == 0 || ncl != pc) && j + 1 < my) {
-        const char* e = reinterpret_cast<const char*>(a.ctab + ((long long)q * a.ncell + ncl) * CELL_TAB);
-        prefetch_l1(e);
-        prefetch_l1(e + 128);
-        prefetch_l1(e + 256);
-        if (GRAD) prefetch_l1(a.cell_lab + ncl);
-      }
-    }
     const int p = (t0 + j * tstep) * TS_NT + tid;
     bool valid = p < a.npix;
     if (CELLS) {
@@ -480,6 +468,18 @@ __global__ void __launch_bounds__(TS_NT, 512 / TS_NT)
     if (GRAD) {
       if (!valid) kd = kt = ks = -1;
       warp_run_add3(gacc, kd, g0, gacc + a.Kd, kt, g1, gacc + a.Kd + a.KT, ks, g2);
+    }
+    if (CELLS && j + 1 < my) {
+      // the next tile's cells (their indices arrived during this tile): the first lane of each run
+      // of equal cells asks L1 for the cell's table entry (3 lines) and labels
+      const int pc = __shfl_up_sync(0xffffffffu, ncl, 1);
+      if (lane == 0 || ncl != pc) {
+        const char* e = reinterpret_cast<const char*>(a.ctab + ((long long)q * a.ncell + ncl) * CELL_TAB);
+        prefetch_l1(e);
+        prefetch_l1(e + 128);
+        prefetch_l1(e + 256);
+        if (GRAD) prefetch_l1(a.cell_lab + ncl);
+      }
     }
   }
   if (timed_out) {
