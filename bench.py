@@ -45,11 +45,13 @@ FLOPS_PER_PIXEL_EVAL = 1000  # FP32 operations of one pixel's chi2 + gradient (F
 # kernel has been captured since its last change): the persistent fit per cell evaluation, the
 # streaming kernel per pixel evaluation (full-sky nside-64 case, 100 realizations).
 TRAFFIC_FIT_PER_CELL_EVAL = None
-TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": None, "L": None, "L_and_grad_unplanned": 129.5,
-                            "L_unplanned": 129.5}
+TRAFFIC_STREAM_PER_PIXEL = {"L_and_grad": 133.4, "L": 132.9, "L_and_grad_unplanned": 130.3,
+                            "L_unplanned": 130.1}
 TRAFFIC_CAPTURE = {"fit": None,
                    "stream": "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_spectral_tma, "
-                             "full-sky nside 64, 100 realizations, per pixel evaluation"}
+                             "full-sky nside 64, 40 realizations (profile_cases stream 40; 252 MB "
+                             "of data, streamed, so traffic scales with the pixels), per pixel "
+                             "evaluation"}
 
 
 def fp32_peak_tflops(sm_mhz):

@@ -70,11 +70,18 @@ def _pipeline64():
     return workloads.scan_subset([937, 1739], nside=64, nconf=4000, kmax=1000, nreal=1)
 
 
+def _fullsky64():
+    """Full sky at nside 64, K = (100, 20, 30), 100 realizations (the fit and W d workload)."""
+    from synth import workloads
+    return workloads.fullsky(64, (100, 20, 30), nreal=100)
+
+
 CASES = {
     "scan64": (_scan64, _scan64_picks),
     "scan16_k1000": (_scan16, _scan16_picks),
     "multires16": (_multires16, lambda wl: [0, 1]),
     "pipeline64": (_pipeline64, lambda wl: [0, 1]),
+    "fullsky64": (_fullsky64, lambda wl: [0, 57]),
 }
 
 

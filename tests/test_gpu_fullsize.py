@@ -54,6 +54,40 @@ def test_fullsky_nside64_hundred_realizations(csx):
         assert_grad_close(g[r], gr, Sr)
 
 
+def test_fullsky_nside64_fit_and_reconstruction(csx):
+    """The full-sky nside-64 workload (K = (100, 20, 30), 100 realizations): one batched fit of all
+    100 realizations, then W d at the fitted points. Two realizations against stored oracle fits
+    (tests/golden/make_fit_refs.py, case fullsky64), and the reconstruction of one of them against
+    the oracle's W d, sigma^2 and r_sys at the GPU's fitted point."""
+    import os
+    from oracle import reconstruct as rc
+    from tests.golden import make_fit_refs as mk
+    if not os.path.exists(os.path.join(os.path.dirname(mk.__file__), "fit_refs_fullsky64.npz")):
+        pytest.skip("stored oracle fits of the full-sky case not written")
+    wl = workloads.fullsky(64, (100, 20, 30), nreal=100)
+    case = Case(wl, "separable")
+    model, sky, labels = case.gpu()
+    beta0 = torch.tensor(pack(wl, [wl.beta0(0) for _ in range(wl.nreal)]), device="cuda")
+    res = csx.fit_batch(model, sky, labels, wl.K, beta0)
+    fg = torch.from_numpy(case.fg32).to("cuda")
+    out = csx.reconstruct(model, sky, labels, wl.K, res["beta"], d_fg=fg, s_hat=True, sigma2=True,
+                          r_sys=True)
+    torch.cuda.synchronize()
+    assert (res["status"].cpu().numpy() == 0).all()
+    picks, refs = stored_refs("fullsky64", case)
+    _sampled_fit_check(csx, case, res, picks, max_alternative=0, refs=refs)
+    P = int(wl.K[0].sum())
+    q = picks[1]
+    b = res["beta"].cpu().numpy()[q * P:(q + 1) * P].astype(np.float64)
+    s = rc.reconstruct(case.nu, case.d64(q), case.ninv64, wl.labels[0], wl.K[0], b)
+    sv = rc.stat_variance(case.nu, case.ninv64, wl.labels[0], wl.K[0], b)
+    rs = rc.systematic_residual(case.nu, case.fg64(), case.ninv64, wl.labels[0], wl.K[0], b)
+    np.testing.assert_allclose(out["s_hat"][q].cpu().numpy(), s, rtol=0, atol=1e-4 * np.abs(s).max())
+    np.testing.assert_allclose(out["sigma2"][q].cpu().numpy(), sv, rtol=1e-4)
+    np.testing.assert_allclose(out["r_sys"][q].cpu().numpy(), rs, rtol=0,
+                               atol=1e-4 * np.abs(rs).max() + 1e-6)
+
+
 def test_gradcheck_nside128_autograd_64_points(csx):
     """The differentiation check at nside 128 (196608 pixels, K = 256 per parameter, P = 768): the
     autograd function's gradient in FP32 and in all-FP64 at 64 random points against the FP64
