@@ -142,40 +142,33 @@ __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, floa
 // reads one line per entry at a compile-time offset):
 //   mom[((cell / 32) * 171 + e(i,j)) * 32 + cell % 32],  e(i,j) = i (35 - i) / 2 + j,
 //   0 <= i <= j < 18   (171 entries).
-// Since d = A_r s + r exactly, S_c = sum w d d^T = A_r Q A_r^T + A_r C^T + C A_r^T + R, but every stored
+// Since d = A_r s + r (to the rounding of r), S_c = sum w d d^T = A_r Q A_r^T + A_r C^T + C A_r^T + R, but every stored
 // block is small where it has to be: R and C carry residuals, not the foreground signal.
 //
 // One warp per cell. Phase 1, lane = pixel: the cell's Gram-Schmidt basis of A_r (computed once per
 // cell, the noise weight w_p scales out of s and r), then s by back-substitution and r = d - A_r s
-// formed without the data's rounding (resid_exact) of up to 32 pixels into shared memory. Phase 2: lanes = 15 upper 4x4 blocks of the 20x20 (zero-padded) v v^T x 2 pixel groups;
+// (ORDERED: FMAs in order of decreasing foreground, resid_fma; else in the Gram-Schmidt basis) of up
+// to 32 pixels into shared memory. Phase 2: lanes = 15 upper 4x4 blocks of the 20x20 (zero-padded)
+// v v^T x 2 pixel groups;
 // partial sums are flushed every 16 pixels to bound FP32 rounding growth. Also sum w d^T n d.
 constexpr int NM = 171;          // stored moment entries per cell
 constexpr int VROW = 44;         // shared floats per pixel: v_Q[20], v_U[20], w (16-byte rows)
 constexpr int BUILD_SMEM_PER_WARP = 32 * VROW + 64;  // pixel rows + the cell's basis and columns
 
-// d - (s0 + a1 s1 + a2 s2) for FP32 inputs, rounded once: the products are split exactly (FMA
-// residue) and the sum is carried with its rounding errors (TwoSum), so the signal-sized terms cancel
-// without leaving their rounding in the small result. The reference-point decomposition
-// d = A_r s + r of the cell moments is then exact to the rounding of r itself, and the gradient
-// formed from the moments at the reference point is as accurate as the residuals, not the data.
-// (__fmul_rn / __fadd_rn are never contracted into FMAs, which would break the error terms.)
-__device__ __forceinline__ void two_sum_acc(float& x, float b, float& err) {
-  const float sum = __fadd_rn(x, b);
-  const float bb = __fsub_rn(sum, x);
-  err = __fadd_rn(err, __fadd_rn(__fsub_rn(x, __fsub_rn(sum, bb)), __fsub_rn(b, bb)));
-  x = sum;
+// d - (s0 + a1 s1 + a2 s2) with FMAs: the larger of the two foreground products first, then the
+// smaller, then s0. Each step rounds once, at the scale of what is left (s0, the smaller
+// foreground and r after the first; s0 and r after the second; r after the last), so the error is
+// about u (|s0| + min(|a1 s1|, |a2 s2|) + |r|) instead of the plain form's u |d|: the moments'
+// decomposition d = A_r s + r then holds to rounding at the scale of the CMB and the fainter
+// foreground, not of the brightest foreground, and so does the gradient formed from the moments
+// at the reference point.
+__device__ __forceinline__ float resid_fma(float d, float s0, float s1, float s2, float a1,
+                                           float a2) {
+  const bool dust_first = fabsf(a1 * s1) >= fabsf(a2 * s2);
+  const float ab = dust_first ? a1 : a2, sb = dust_first ? s1 : s2;
+  const float ac = dust_first ? a2 : a1, sc = dust_first ? s2 : s1;
+  return fmaf(-ac, sc, fmaf(-ab, sb, d)) - s0;
 }
-__device__ __forceinline__ float resid_exact(float d, float s0, float s1, float s2, float a1,
-                                             float a2) {
-  const float p1 = __fmul_rn(a1, s1), e1 = fmaf(a1, s1, -p1);
-  const float p2 = __fmul_rn(a2, s2), e2 = fmaf(a2, s2, -p2);
-  float x = d, err = 0.f;
-  two_sum_acc(x, -p1, err);
-  two_sum_acc(x, -p2, err);
-  two_sum_acc(x, -s0, err);
-  return __fadd_rn(x, __fsub_rn(err, __fadd_rn(e1, e2)));
-}
-
 
 __device__ __forceinline__ int mom_index(int i, int j) { return (i * (35 - i)) / 2 + j; }
 // first entry of the group of 32 cells that holds `cell` (entry e of the cell: [e * 32 + cell % 32])
@@ -190,7 +183,7 @@ constexpr int fit_rows_floats() {
   return PATH == CSX_PATH_MOMENT ? 90 * NT : 0;
 }
 
-template <int NT, bool SEP, bool EXACT>
+template <int NT, bool SEP, bool ORDERED>
 __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* sv = smem + warp * BUILD_SMEM_PER_WARP;  // 32 pixel rows
@@ -266,16 +259,16 @@ __device__ double build_moments(const FitArgs& a, Ctx& c, float* smem, Shared& s
         dnd += (double)(wp * pd);
         tq0 *= g.i0; tq1 *= g.i1; tq2 *= g.i2;
         tu0 *= g.i0; tu1 *= g.i1; tu2 *= g.i2;
-        // s = R^-1 t (Gram-Schmidt back-substitution), then r = d - A_r s exactly for this s
+        // s = R^-1 t (Gram-Schmidt back-substitution), then r = d - A_r s for this s
         const float sq1 = fmaf(-g.nu, tq2, tq1), su1 = fmaf(-g.nu, tu2, tu1);
         const float sq0 = tq0 - g.mu1 * sq1 - g.mu2 * tq2;
         const float su0 = tu0 - g.mu1 * su1 - g.mu2 * tu2;
 #pragma unroll
         for (int f = 0; f < NB; ++f) {
-          if (EXACT) {
+          if (ORDERED) {
             const float a1 = sb[32 + f], a2 = sb[48 + f];
-            row[f] = (f < 15) ? resid_exact(dq[f], sq0, sq1, tq2, a1, a2) : 0.f;
-            row[20 + f] = (f < 15) ? resid_exact(du[f], su0, su1, tu2, a1, a2) : 0.f;
+            row[f] = (f < 15) ? resid_fma(dq[f], sq0, sq1, tq2, a1, a2) : 0.f;
+            row[20 + f] = (f < 15) ? resid_fma(du[f], su0, su1, tu2, a1, a2) : 0.f;
           } else {  // in the Gram-Schmidt basis, rounded at the data's scale
             const float c1 = sb[f], c2 = sb[16 + f];
             row[f] = (f < 15) ? dq[f] - fmaf(tq2, c2, fmaf(tq1, c1, tq0)) : 0.f;
@@ -716,14 +709,14 @@ __device__ void fd_gradient(const FitArgs& a, Ctx& c, Shared& sh, const float* z
 // Moment path: make the current point c.x the reference point and rebuild the cell moments. The
 // first build of a fit (at the start point, far from the optimum) forms the residuals in the
 // Gram-Schmidt basis; every later one (a move of the reference point near convergence) forms them
-// exactly (resid_exact), which the precision of the last iterations' gradients rests on.
+// with the ordered FMAs of resid_fma, which the precision of the last iterations' gradients rests on.
 template <int NT, int NOISE>
-__device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem, bool exact = true) {
+__device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem, bool ordered = true) {
   for (int i = threadIdx.x; i < c.P; i += NT) c.xr[i] = c.x[i];
   __syncthreads();
   fill_tables<NT>(a, c, c.xr, c.tabr);
   constexpr bool SEP = NOISE == CSX_NOISE_SEPARABLE;
-  return exact ? build_moments<NT, SEP, true>(a, c, smem, sh)
+  return ordered ? build_moments<NT, SEP, true>(a, c, smem, sh)
                : build_moments<NT, SEP, false>(a, c, smem, sh);
 }
 
