@@ -720,6 +720,89 @@ __device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem, bo
                : build_moments<NT, SEP, false>(a, c, smem, sh);
 }
 
+// The two-loop recursion of L-BFGS with this thread's elements of p in registers (P <= TL_E NT)
+// and the next pair of history vectors loaded while the current dot product is being reduced:
+// the operations and their order are those of the loops over the slot vectors in fit_problem
+// (elements beyond P are zeros and add exact zeros), so the direction has the same bits.
+constexpr int TL_E = 12;
+template <int NT>
+__device__ __forceinline__ void two_loop_reg(const FitArgs& a, Ctx& c, Shared& sh, int P, int m,
+                                             int head, int count, float gamma) {
+  const int tid = threadIdx.x;
+  const long long Pm = a.Pmax;
+  float pr[TL_E], u[TL_E], v[TL_E];  // p; the next dot-product and update operands
+#pragma unroll
+  for (int e = 0; e < TL_E; ++e) {
+    const int i = tid + e * NT;
+    pr[e] = i < P ? c.p[i] : 0.f;
+  }
+  auto load = [&](const float* dv, const float* av) {
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) {
+      const int i = tid + e * NT;
+      u[e] = i < P ? dv[i] : 0.f;
+      v[e] = i < P ? av[i] : 0.f;
+    }
+  };
+  if (count > 0) {
+    const int k = (head - 1 + m) % m;
+    load(c.S + k * Pm, c.Y + k * Pm);
+  }
+  for (int j = 0; j < count; ++j) {
+    const int k = (head - 1 - j + m) % m;
+    float sv[TL_E], yv[TL_E];
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) {
+      sv[e] = u[e];
+      yv[e] = v[e];
+    }
+    if (j + 1 < count) {
+      const int kn = (head - 2 - j + m) % m;
+      load(c.S + kn * Pm, c.Y + kn * Pm);
+    }
+    float dotf = 0.f;
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) dotf = fmaf(sv[e], pr[e], dotf);
+    const double dot = block_sum_f<NT>(dotf, sh.red);
+    const double al = sh.rho[k] * dot;
+    if (tid == 0) sh.alpha[k] = al;
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) pr[e] -= (float)al * yv[e];
+  }
+#pragma unroll
+  for (int e = 0; e < TL_E; ++e) pr[e] *= gamma;
+  if (count > 0) {
+    const int k = (head - count + m) % m;  // j = count - 1
+    load(c.Y + k * Pm, c.S + k * Pm);
+  }
+  for (int j = count - 1; j >= 0; --j) {
+    const int k = (head - 1 - j + m) % m;
+    float yv[TL_E], sv[TL_E];
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) {
+      yv[e] = u[e];
+      sv[e] = v[e];
+    }
+    if (j > 0) {
+      const int kn = (head - j + m) % m;  // j - 1
+      load(c.Y + kn * Pm, c.S + kn * Pm);
+    }
+    float dotf = 0.f;
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) dotf = fmaf(yv[e], pr[e], dotf);
+    const double dot = block_sum_f<NT>(dotf, sh.red);
+    const double be = sh.rho[k] * dot;
+    const float coef = (float)(sh.alpha[k] - be);
+#pragma unroll
+    for (int e = 0; e < TL_E; ++e) pr[e] += coef * sv[e];
+  }
+#pragma unroll
+  for (int e = 0; e < TL_E; ++e) {
+    const int i = tid + e * NT;
+    if (i < P) c.p[i] = pr[e];
+  }
+}
+
 template <int NT, int PATH, int GMODE, int NOISE>
 __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, int q,
                             long long poff) {
@@ -779,28 +862,32 @@ __device__ void fit_problem(const FitArgs& a, Ctx& c, Shared& sh, float* smem, i
       const bool act = (c.z[i] <= zl && gi > 0.f) || (c.z[i] >= zu && gi < 0.f);
       c.p[i] = act ? 0.f : gi;
     }
-    for (int j = 0; j < count; ++j) {
-      const int k = (head - 1 - j + m) % m;
-      const float* Sk = c.S + (long long)k * a.Pmax;
-      float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
-      for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
-      const double dot = block_sum_f<NT>(dotf, sh.red);
-      const double al = sh.rho[k] * dot;
-      if (tid == 0) sh.alpha[k] = al;
-      const float* Yk = c.Y + (long long)k * a.Pmax;
-      for (int i = tid; i < P; i += NT) c.p[i] -= (float)al * Yk[i];
-    }
-    for (int i = tid; i < P; i += NT) c.p[i] *= (float)gamma;
-    for (int j = count - 1; j >= 0; --j) {
-      const int k = (head - 1 - j + m) % m;
-      const float* Yk = c.Y + (long long)k * a.Pmax;
-      float dotf = 0.f;
-      for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
-      const double dot = block_sum_f<NT>(dotf, sh.red);
-      const double be = sh.rho[k] * dot;
-      const float* Sk = c.S + (long long)k * a.Pmax;
-      const float coef = (float)(sh.alpha[k] - be);
-      for (int i = tid; i < P; i += NT) c.p[i] += coef * Sk[i];
+    if (P <= TL_E * NT) {
+      two_loop_reg<NT>(a, c, sh, P, m, head, count, (float)gamma);
+    } else {
+      for (int j = 0; j < count; ++j) {
+        const int k = (head - 1 - j + m) % m;
+        const float* Sk = c.S + (long long)k * a.Pmax;
+        float dotf = 0.f;  // per-thread partial in FP32 (a few terms), FP64 across the block
+        for (int i = tid; i < P; i += NT) dotf = fmaf(Sk[i], c.p[i], dotf);
+        const double dot = block_sum_f<NT>(dotf, sh.red);
+        const double al = sh.rho[k] * dot;
+        if (tid == 0) sh.alpha[k] = al;
+        const float* Yk = c.Y + (long long)k * a.Pmax;
+        for (int i = tid; i < P; i += NT) c.p[i] -= (float)al * Yk[i];
+      }
+      for (int i = tid; i < P; i += NT) c.p[i] *= (float)gamma;
+      for (int j = count - 1; j >= 0; --j) {
+        const int k = (head - 1 - j + m) % m;
+        const float* Yk = c.Y + (long long)k * a.Pmax;
+        float dotf = 0.f;
+        for (int i = tid; i < P; i += NT) dotf = fmaf(Yk[i], c.p[i], dotf);
+        const double dot = block_sum_f<NT>(dotf, sh.red);
+        const double be = sh.rho[k] * dot;
+        const float* Sk = c.S + (long long)k * a.Pmax;
+        const float coef = (float)(sh.alpha[k] - be);
+        for (int i = tid; i < P; i += NT) c.p[i] += coef * Sk[i];
+      }
     }
     // negate, mask the active set and outward steps at a bound, directional derivative, QN step
     float gpf = 0.f;
