@@ -165,3 +165,26 @@ def test_patch_counts_are_bounded_on_the_host(lib):
     rc = lib.csx_cell_like_grad(ctypes.byref(model.c), ctypes.byref(sky), ok, small, 1, ok, ok, ok,
                                 ok, None)
     assert rc == -1 and b"homogeneous or separable" in lib.csx_last_error()
+
+
+def test_spectral_plan_arguments_are_refused_on_the_host(lib):
+    """The cell plan's entry points check their arguments before touching a device; destroying
+    NULL is a no-op. The pointers below are never dereferenced."""
+    import ctypes
+    plan = ctypes.c_void_p()
+    ok = ctypes.c_void_p(0x10000)
+    K = (ctypes.c_int32 * 3)(4, 2, 3)
+    rc = lib.csx_spectral_plan_create(-1, ok, K, None, ctypes.byref(plan))
+    assert rc == -1 and b"npix" in lib.csx_last_error() and not plan.value
+    big = (ctypes.c_int32 * 3)(2 ** 31 - 1, 2 ** 30, 2)
+    rc = lib.csx_spectral_plan_create(10, ok, big, None, ctypes.byref(plan))
+    assert rc == -1 and b"K_j" in lib.csx_last_error() and not plan.value
+    rc = lib.csx_spectral_plan_create(10, None, K, None, ctypes.byref(plan))
+    assert rc == -1 and b"labels is NULL" in lib.csx_last_error()
+    rc = lib.csx_spectral_plan_create(10, ok, K, None, None)
+    assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
+    n = ctypes.c_int32()
+    assert lib.csx_spectral_plan_ncell(None, ctypes.byref(n)) == -1
+    rc = lib.csx_spectral_grad_plan(None, None, None, 1, ok, ok, ok, None)
+    assert rc == -1 and b"plan is NULL" in lib.csx_last_error()
+    assert lib.csx_spectral_plan_destroy(None) == 0
