@@ -478,7 +478,11 @@ def run_csx(args):
         if dist:
             dist.destroy_process_group()
         return
-    launches_per_step = 4 + (1 if path == "moment" else 0)
+    # the library kernels one step launches: fit descriptors, queue order (up to 16384
+    # configurations), cells (moment path) and the fit; reconstruction descriptors, tables and
+    # reconstruction; the selection (and the global selection when N > 1)
+    launches_per_step = (2 + (1 if nconf <= 16384 else 0) + (1 if path == "moment" else 0) + 3 + 1
+                         + (1 if dist else 0))
     # DRAM traffic of one fit launch from the ncu capture (moment path only), scaled by units
     # the DRAM traffic per cell evaluation was captured with 128-thread CTAs
     traffic = (TRAFFIC_FIT_PER_CELL_EVAL * unit_evals
