@@ -100,8 +100,16 @@ __device__ __forceinline__ int ptype(const Ctx& c, int i) {
 // ------------------------------------------------------------------------------ tables ----------
 // The rows of table_entry; a dust-temperature patch's B and dlnB/dT entries of a band are formed by
 // one thread from the same two expm1 values: with E = e^x - 1, x / (1 - e^-x) = x (1 + E) / E.
-template <int NT>
+// STAGE (moment path): the parameters are first copied, coalesced, into the shared memory of the
+// evaluation rows or the build staging (free until the tables are formed), so that each entry's
+// read of its parameter is a shared-memory load rather than a dependent global one.
+template <int NT, bool STAGE = false>
 __device__ void fill_tables(const FitArgs& a, const Ctx& c, const float* x, float* tab) {
+  if (STAGE && c.P <= 90 * NT) {
+    for (int i = threadIdx.x; i < c.P; i += NT) c.smem[i] = x[i];
+    __syncthreads();
+    x = c.smem;
+  }
   const int nd = c.Kd * NB, nt = c.KT * NB, n = nd + nt + c.Ks * NB;
   const Bands& b = a.bands;
   for (int i = threadIdx.x; i < n; i += NT) {
@@ -360,7 +368,7 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
   if ((threadIdx.x & 31) == 0 && (threadIdx.x & ~31) < c.ncell)
     prefetch_l2(c.mom + mom_group(threadIdx.x & ~31), GROUP_BYTES);
   partials_zero<NT>(c, WANT_H);
-  fill_tables<NT>(a, c, c.x, c.tab);  // ends with a barrier
+  fill_tables<NT, true>(a, c, c.x, c.tab);  // ends with a barrier
   const float* nb = a.ninv_band;
   float nsum = 0.f;
 #pragma unroll
@@ -714,7 +722,7 @@ template <int NT, int NOISE>
 __device__ double recentre(const FitArgs& a, Ctx& c, Shared& sh, float* smem, bool ordered = true) {
   for (int i = threadIdx.x; i < c.P; i += NT) c.xr[i] = c.x[i];
   __syncthreads();
-  fill_tables<NT>(a, c, c.xr, c.tabr);
+  fill_tables<NT, true>(a, c, c.xr, c.tabr);
   constexpr bool SEP = NOISE == CSX_NOISE_SEPARABLE;
   return ordered ? build_moments<NT, SEP, true>(a, c, smem, sh)
                : build_moments<NT, SEP, false>(a, c, smem, sh);
