@@ -10,6 +10,11 @@
 //               smallest best dot product (stable order: the i-th emptied cluster takes the i-th),
 //               renormalised by sqrt((x x + y y) + z z) (a zero norm counts as 1);
 //   labels:     renumbered 0..K_eff-1 in order of first appearance.
+// The assignment screens the clusters in FP32 first (B300's FP64 rate is a small fraction of its
+// FP32 rate): with unit vectors the FP32 dot product is within 3e-7 of the FP64 one, so every
+// cluster whose FP32 value is within KM_SCREEN of the FP32 maximum is evaluated in FP64 as above
+// (in index order, the first of equal maxima kept), which contains the FP64 maximum: the labels
+// stay bit-exact.
 // K >= n gives one pixel per patch and K <= 1 a single patch, as in the generator.
 #include <cmath>
 
@@ -19,6 +24,12 @@ namespace csx {
 
 constexpr int KM_NT = 256;
 constexpr int KM_KMAX = KMEANS_KMAX;  // clusters per labeling (centroids, sums in shared memory)
+constexpr float KM_SCREEN = 2e-6f;    // twice a bound of |FP32 - FP64| dot product (1e-6 > 3e-7)
+
+// float4 copies of the centroids follow the double arrays, 16-byte aligned
+__host__ __device__ constexpr size_t km_f4_offset(int kmax) {
+  return ((size_t)kmax * (6 * sizeof(double) + sizeof(int)) + 15) & ~size_t(15);
+}
 
 __device__ __forceinline__ double km_dot(double x, double y, double z, double cx, double cy,
                                          double cz) {
@@ -53,12 +64,14 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
   double* cent = km_smem;             // [K][3]
   double* sums = km_smem + 3 * K;     // [K][3]
   int* cnt = reinterpret_cast<int*>(km_smem + 6 * K);  // [K]
+  float4* cf = reinterpret_cast<float4*>(reinterpret_cast<char*>(km_smem) + km_f4_offset(K));
   const int* init = a.init + a.ioff[L];
   for (int k = tid; k < K; k += KM_NT) {
     const int p = init[k];
     cent[3 * k] = a.vec[3 * p];
     cent[3 * k + 1] = a.vec[3 * p + 1];
     cent[3 * k + 2] = a.vec[3 * p + 2];
+    cf[k] = make_float4((float)cent[3 * k], (float)cent[3 * k + 1], (float)cent[3 * k + 2], 0.f);
   }
   __syncthreads();
   int it = 0;
@@ -67,13 +80,23 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
     int changed = 0;
     for (int p = tid; p < n; p += KM_NT) {
       const double x = a.vec[3 * p], y = a.vec[3 * p + 1], z = a.vec[3 * p + 2];
+      const float xf = (float)x, yf = (float)y, zf = (float)z;
+      float b32 = -INFINITY;
+      for (int k = 0; k < K; ++k) {
+        const float4 c = cf[k];
+        b32 = fmaxf(b32, fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x)));
+      }
+      const float thr = b32 - KM_SCREEN;
       double bv = -INFINITY;
       int bk = 0;
       for (int k = 0; k < K; ++k) {
-        const double v = km_dot(x, y, z, cent[3 * k], cent[3 * k + 1], cent[3 * k + 2]);
-        if (v > bv) {
-          bv = v;
-          bk = k;
+        const float4 c = cf[k];
+        if (fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x)) >= thr) {
+          const double v = km_dot(x, y, z, cent[3 * k], cent[3 * k + 1], cent[3 * k + 2]);
+          if (v > bv) {
+            bv = v;
+            bk = k;
+          }
         }
       }
       if (it == 0 || lab[p] != bk) changed = 1;
@@ -154,6 +177,7 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
       cent[3 * k] = __ddiv_rn(x, nr);
       cent[3 * k + 1] = __ddiv_rn(y, nr);
       cent[3 * k + 2] = __ddiv_rn(z, nr);
+      cf[k] = make_float4((float)cent[3 * k], (float)cent[3 * k + 1], (float)cent[3 * k + 2], 0.f);
     }
     __syncthreads();
   }
@@ -175,7 +199,7 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
   for (int p = tid; p < n; p += KM_NT) lab[p] = remap[lab[p]];
 }
 
-size_t kmeans_smem(int kmax) { return (size_t)kmax * (6 * sizeof(double) + sizeof(int)); }
+size_t kmeans_smem(int kmax) { return km_f4_offset(kmax) + (size_t)kmax * sizeof(float4); }
 
 int launch_kmeans(const double* vec, int n, int nlab, const int* K_dev, const long long* ioff_dev,
                   const int* init, int max_iter, int kmax, int* labels, double* best, int* iters,
