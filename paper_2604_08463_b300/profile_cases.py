@@ -5,6 +5,9 @@ device at most, inputs larger than L2), printed with the unit counts a roofline 
         the persistent fit (k_fit, moment path, 128 threads) on the first NCONF configurations of
         the nside-64 scan (|b| > 20 deg, K per parameter log-uniform up to KMAX, 10 realizations,
         seed 4), fitted twice from the start point; prints the cell evaluations of one fit
+    python -m paper_2604_08463_b300.profile_cases kmeans NCONF KMAX
+        the GPU spherical K-means of every distinct K of that scan's first NCONF configurations
+        (one launch, twice)
     python -m paper_2604_08463_b300.profile_cases stream NREAL
         the streaming kernel (k_spectral_tma) on the full-sky nside-64 configuration with
         K = (100, 20, 30) and separable noise, NREAL realizations: plan L + grad, plan L,
@@ -74,11 +77,30 @@ def stream_case(nreal: int):
     plan.close()
 
 
+def kmeans_case(nconf: int, kmax: int):
+    import torch
+    from synth import healpix, kmeans as km, workloads
+    from . import csx
+    pix = healpix.galactic_cut(64, 20.0)
+    vec = healpix.unit_vectors(64)[pix]
+    n = vec.shape[0]
+    ks = sorted({int(k) for k in workloads.sample_patch_counts(nconf, kmax, seed=4).reshape(-1)})
+    init = [km.init_indices(n, k, 100 + k) for k in ks if 1 < k < n]
+    vd = torch.from_numpy(vec).to(torch.device("cuda", torch.cuda.current_device()))
+    for _ in range(2):
+        lab, iters = csx.kmeans(vd, ks, init)
+        torch.cuda.synchronize()
+    print("labelings %d (K %d..%d) pixels %d mean iterations %.1f"
+          % (len(ks), ks[0], ks[-1], n, float(iters.float().mean())))
+
+
 def main(argv):
     if len(argv) >= 1 and argv[0] == "fit":
         fit_case(int(argv[1]) if len(argv) > 1 else 60, int(argv[2]) if len(argv) > 2 else 500)
     elif len(argv) >= 1 and argv[0] == "stream":
         stream_case(int(argv[1]) if len(argv) > 1 else 40)
+    elif len(argv) >= 1 and argv[0] == "kmeans":
+        kmeans_case(int(argv[1]) if len(argv) > 1 else 1000, int(argv[2]) if len(argv) > 2 else 500)
     else:
         print(__doc__)
         return 2
