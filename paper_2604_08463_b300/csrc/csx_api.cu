@@ -897,16 +897,19 @@ int csx_kmeans(const double* vec, int32_t n, int32_t nlab, const int32_t* K, con
   int rc = CSX_OK;
   const size_t best_b = (size_t)nlab * n * sizeof(double);
   const size_t k_b = ((size_t)nlab * sizeof(int) + 15) & ~size_t(15);
-  char* scr = (char*)scratch(SCR_KMEANS, best_b + k_b + (size_t)nlab * sizeof(long long), &rc);
+  const size_t mem_b = ((size_t)nlab * n * sizeof(int) + 15) & ~size_t(15);
+  char* scr = (char*)scratch(SCR_KMEANS, best_b + mem_b + k_b + (size_t)nlab * sizeof(long long), &rc);
   if (rc) return rc;
   double* best = (double*)scr;
-  int* K_dev = (int*)(scr + best_b);
-  long long* ioff_dev = (long long*)(scr + best_b + k_b);
+  int* members = (int*)(scr + best_b);
+  int* K_dev = (int*)(scr + best_b + mem_b);
+  long long* ioff_dev = (long long*)(scr + best_b + mem_b + k_b);
   cudaStream_t s = (cudaStream_t)stream;
   CSX_CUDA(cudaMemcpyAsync(K_dev, K, (size_t)nlab * sizeof(int), cudaMemcpyHostToDevice, s));
   CSX_CUDA(cudaMemcpyAsync(ioff_dev, ioff.data(), (size_t)nlab * sizeof(long long),
                            cudaMemcpyHostToDevice, s));
-  return launch_kmeans(vec, n, nlab, K_dev, ioff_dev, init, max_iter, kmax, labels, best, iters, s);
+  return launch_kmeans(vec, n, nlab, K_dev, ioff_dev, init, max_iter, kmax, labels, best, members,
+                       iters, s);
 }
 
 int csx_select(int32_t nconf, int32_t nreal, const double* metrics, double* vtot, int32_t* best,

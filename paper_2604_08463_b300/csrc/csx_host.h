@@ -121,8 +121,8 @@ int launch_fit_desc(int nconf, int nreal, const int* K_dev, ProbDesc* probs, cud
 constexpr int KMEANS_KMAX = 2048;
 size_t kmeans_smem(int kmax);
 int launch_kmeans(const double* vec, int n, int nlab, const int* K_dev, const long long* ioff_dev,
-                  const int* init, int max_iter, int kmax, int* labels, double* best, int* iters,
-                  cudaStream_t s);
+                  const int* init, int max_iter, int kmax, int* labels, double* best, int* members,
+                  int* iters, cudaStream_t s);
 
 struct FitArgs {
   Bands bands;

@@ -5,8 +5,10 @@
 //   assignment: the largest dot product (x cx + y cy) + z cz (each product and sum rounded once,
 //               no fused multiply-add), the first cluster on ties;
 //   stop:       when an assignment repeats the previous one, or after max_iter assignments;
-//   centroids:  member sums accumulated in increasing pixel order (one thread owns a cluster and
-//               walks the pixels in order), an emptied cluster re-seeded at the pixel with the
+//   centroids:  member sums accumulated in increasing pixel order (the pixels are placed in a
+//               list grouped by cluster, in pixel order within a cluster, by one warp walking
+//               them in order; the thread owning a cluster then adds its members), an emptied
+//               cluster re-seeded at the pixel with the
 //               smallest best dot product (stable order: the i-th emptied cluster takes the i-th),
 //               renormalised by sqrt((x x + y y) + z z) (a zero norm counts as 1);
 //   labels:     renumbered 0..K_eff-1 in order of first appearance.
@@ -28,7 +30,7 @@ constexpr float KM_SCREEN = 2e-6f;    // twice a bound of |FP32 - FP64| dot prod
 
 // float4 copies of the centroids follow the double arrays, 16-byte aligned
 __host__ __device__ constexpr size_t km_f4_offset(int kmax) {
-  return ((size_t)kmax * (6 * sizeof(double) + sizeof(int)) + 15) & ~size_t(15);
+  return ((size_t)kmax * (6 * sizeof(double) + 2 * sizeof(int)) + 15) & ~size_t(15);
 }
 
 __device__ __forceinline__ double km_dot(double x, double y, double z, double cx, double cy,
@@ -44,6 +46,7 @@ struct KmArgs {
   const int* init;       // concatenated starting pixels
   int* labels;           // [nlab][n] (output; also the working assignment)
   double* best;          // [nlab][n] scratch
+  int* members;          // [nlab][n] scratch: pixels grouped by cluster
   int* iters;            // [nlab] or NULL
 };
 
@@ -56,6 +59,7 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
   const int K = a.K[L];
   int* lab = a.labels + (long long)L * n;
   double* best = a.best + (long long)L * n;
+  int* members = a.members + (long long)L * n;
   if (K <= 1 || K >= n) {
     for (int p = tid; p < n; p += KM_NT) lab[p] = (K <= 1) ? 0 : p;
     if (a.iters && tid == 0) a.iters[L] = 0;
@@ -106,19 +110,56 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
     changed = __syncthreads_or(changed);
     if (!changed) break;
     // ---- member sums, in pixel order, by the thread owning the cluster ------------------------
-    for (int k = tid; k < K; k += KM_NT) {
-      sums[3 * k] = sums[3 * k + 1] = sums[3 * k + 2] = 0.0;
-      cnt[k] = 0;
+    // counts, then each cluster's start in the member list (warp 0: an exclusive scan over K)
+    int* cur = cnt + K;  // [K] placement cursor
+    for (int k = tid; k < K; k += KM_NT) cnt[k] = 0;
+    __syncthreads();
+    for (int p = tid; p < n; p += KM_NT) atomicAdd(&cnt[lab[p]], 1);
+    __syncthreads();
+    if (tid < 32) {
+      const int per = (K + 31) / 32, k0 = min(K, tid * per), k1 = min(K, k0 + per);
+      int tot = 0;
+      for (int k = k0; k < k1; ++k) tot += cnt[k];
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += y;
+      }
+      int run = incl - tot;
+      for (int k = k0; k < k1; ++k) {
+        cur[k] = run;
+        run += cnt[k];
+      }
+      __syncwarp();
+      // placement in pixel order: lanes with equal labels take consecutive slots, lowest lane first
+      for (int base = 0; base < n; base += 32) {
+        const int p = base + tid;
+        const int l = p < n ? lab[p] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, l);
+        const int rank = __popc(grp & ((1u << tid) - 1u));
+        const int c0 = (l >= 0) ? cur[l] : 0;
+        __syncwarp();
+        if (l >= 0) {
+          members[c0 + rank] = p;
+          if (rank == 0) cur[l] = c0 + __popc(grp);
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
-    for (int p = 0; p < n; ++p) {
-      const int l = lab[p];  // the same address for every thread: one broadcast load
-      if (l % KM_NT == tid) {
-        sums[3 * l] = __dadd_rn(sums[3 * l], a.vec[3 * p]);
-        sums[3 * l + 1] = __dadd_rn(sums[3 * l + 1], a.vec[3 * p + 1]);
-        sums[3 * l + 2] = __dadd_rn(sums[3 * l + 2], a.vec[3 * p + 2]);
-        ++cnt[l];
+    for (int k = tid; k < K; k += KM_NT) {
+      const int e = cur[k], b = e - cnt[k];
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      for (int i = b; i < e; ++i) {
+        const int p = members[i];
+        sx = __dadd_rn(sx, a.vec[3 * p]);
+        sy = __dadd_rn(sy, a.vec[3 * p + 1]);
+        sz = __dadd_rn(sz, a.vec[3 * p + 2]);
       }
+      sums[3 * k] = sx;
+      sums[3 * k + 1] = sy;
+      sums[3 * k + 2] = sz;
     }
     __syncthreads();
     // ---- emptied clusters, in index order, take the pixels of smallest best value ---------------
@@ -202,8 +243,8 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
 size_t kmeans_smem(int kmax) { return km_f4_offset(kmax) + (size_t)kmax * sizeof(float4); }
 
 int launch_kmeans(const double* vec, int n, int nlab, const int* K_dev, const long long* ioff_dev,
-                  const int* init, int max_iter, int kmax, int* labels, double* best, int* iters,
-                  cudaStream_t s) {
+                  const int* init, int max_iter, int kmax, int* labels, double* best, int* members,
+                  int* iters, cudaStream_t s) {
   if (nlab == 0) return CSX_OK;
   KmArgs a;
   a.vec = vec;
@@ -215,6 +256,7 @@ int launch_kmeans(const double* vec, int n, int nlab, const int* K_dev, const lo
   a.init = init;
   a.labels = labels;
   a.best = best;
+  a.members = members;
   a.iters = iters;
   const size_t smem = kmeans_smem(kmax < 1 ? 1 : kmax);
   CSX_CUDA(cudaFuncSetAttribute(k_kmeans, cudaFuncAttributeMaxDynamicSharedMemorySize,
