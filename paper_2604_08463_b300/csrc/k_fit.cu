@@ -468,6 +468,8 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
       D[0] = 0.f;
       D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
       D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
+      row[(60 + f) * NT] = D[1];  // dA is not needed again: the gradient pass reads D back
+      row[(75 + f) * NT] = D[2];
 #pragma unroll
       for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * 32];
 #pragma unroll
@@ -556,11 +558,10 @@ __device__ double eval_moment(const FitArgs& a, Ctx& c, Shared& sh) {
 #pragma unroll 3
     for (int f = 0; f < 15; ++f) {
       const float a1 = row[(30 + f) * NT], a2 = row[(45 + f) * NT];
-      const float e1 = row[(60 + f) * NT], e2 = row[(75 + f) * NT];
       float D[3], C[3];
       D[0] = 0.f;
-      D[1] = fmaf(a2, Yd[2][0], fmaf(a1, Yd[1][0], Yd[0][0])) - e1;
-      D[2] = fmaf(a2, Yd[2][1], fmaf(a1, Yd[1][1], Yd[0][1])) - e2;
+      D[1] = row[(60 + f) * NT];
+      D[2] = row[(75 + f) * NT];
 #pragma unroll
       for (int k = 0; k < 3; ++k) C[k] = ms[mom_index(f, 15 + k) * 32];
       float E[3];
