@@ -85,21 +85,36 @@ __global__ void __launch_bounds__(KM_NT) k_kmeans(const KmArgs a) {
     for (int p = tid; p < n; p += KM_NT) {
       const double x = a.vec[3 * p], y = a.vec[3 * p + 1], z = a.vec[3 * p + 2];
       const float xf = (float)x, yf = (float)y, zf = (float)z;
-      float b32 = -INFINITY;
+      // FP32 maximum and runner-up (the first index of the maximum kept)
+      float b32 = -INFINITY, r32 = -INFINITY;
+      int k32 = 0;
       for (int k = 0; k < K; ++k) {
         const float4 c = cf[k];
-        b32 = fmaxf(b32, fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x)));
+        const float v = fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x));
+        if (v > b32) {
+          r32 = b32;
+          b32 = v;
+          k32 = k;
+        } else {
+          r32 = fmaxf(r32, v);
+        }
       }
       const float thr = b32 - KM_SCREEN;
       double bv = -INFINITY;
       int bk = 0;
-      for (int k = 0; k < K; ++k) {
-        const float4 c = cf[k];
-        if (fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x)) >= thr) {
-          const double v = km_dot(x, y, z, cent[3 * k], cent[3 * k + 1], cent[3 * k + 2]);
-          if (v > bv) {
-            bv = v;
-            bk = k;
+      if (r32 < thr) {
+        // a single candidate: it is the FP64 maximum
+        bk = k32;
+        bv = km_dot(x, y, z, cent[3 * k32], cent[3 * k32 + 1], cent[3 * k32 + 2]);
+      } else {
+        for (int k = 0; k < K; ++k) {
+          const float4 c = cf[k];
+          if (fmaf(zf, c.z, fmaf(yf, c.y, xf * c.x)) >= thr) {
+            const double v = km_dot(x, y, z, cent[3 * k], cent[3 * k + 1], cent[3 * k + 2]);
+            if (v > bv) {
+              bv = v;
+              bk = k;
+            }
           }
         }
       }
